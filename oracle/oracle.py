@@ -1,0 +1,270 @@
+"""ctypes marshalling for the FP64 C oracle (``mp3pcf_oracle.c``). Test infrastructure only.
+
+Every function here converts numpy arrays to pointers and back; all arithmetic is in the C file.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mp3pcf_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, IEEE arithmetic, OpenMP over centres)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-std=gnu11", "-O2", "-fopenmp", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OrcCfg(C.Structure):
+    _fields_ = [("n_bins", C.c_int32), ("theta_min", C.c_double), ("theta_max", C.c_double),
+                ("n_max", C.c_int32), ("n_phi", C.c_int32), ("n_z", C.c_int32),
+                ("quantum", C.c_double), ("norm_truncate", C.c_int32),
+                ("radial_nodes", C.c_int32)]
+
+
+@dataclass
+class Setup:
+    """Measurement setup (bins in arcmin)."""
+    n_bins: int
+    theta_min: float
+    theta_max: float
+    n_max: int
+    n_phi: int = 100
+    n_z: int = 1
+    quantum: float = 2.0 ** -13
+    norm_truncate: int = 0
+    radial_nodes: int = 0
+
+    def c(self) -> OrcCfg:
+        return OrcCfg(self.n_bins, self.theta_min, self.theta_max, self.n_max, self.n_phi,
+                      self.n_z, self.quantum, self.norm_truncate, self.radial_nodes)
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build_oracle())
+        P = C.c_void_p
+        I64 = C.c_int64
+        for name, args in {
+            "orc_edges": [P, P, P],
+            "orc_moments": [P, I64, P, P, P, P, P, P, I64, P, P, P],
+            "orc_count_pairs": [P, I64, P, P, I64, P, P],
+            "orc_contract": [P, P, P, P, P, I64, P, P, P, P, P],
+            "orc_edge_correct": [P, P, P, P, P],
+            "orc_to_gamma": [P, P, C.c_int32, P],
+            "orc_to_map3": [P, P, I64, P, P, P],
+            "orc_filter": [C.c_int32, C.c_double, C.c_double, C.c_double, P, P],
+            "orc_cen_factor": [C.c_int32, C.c_double, C.c_double, C.c_double, P],
+            "orc_combine8": [P, P],
+            "orc_brute": [P, I64, P, P, P, P, P, P, C.c_int32, P, P, P, P, P, P],
+            "orc_num_threads": [],
+        }.items():
+            f = getattr(_lib, name)
+            f.argtypes = args
+            f.restype = C.c_int
+    return _lib
+
+
+def _p(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _check(rc: int, ok=(0,)):
+    if rc not in ok:
+        raise RuntimeError("oracle call failed with status %d" % rc)
+    return rc
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+def edges(s: Setup):
+    e = np.zeros(s.n_bins + 1)
+    e2 = np.zeros(s.n_bins + 1, dtype=np.int64)
+    cfg = s.c()
+    _check(lib().orc_edges(C.byref(cfg), _p(e), _p(e2)))
+    return e, e2
+
+
+def _cat(cat):
+    zb = None if cat.zbin is None else _c(cat.zbin, np.uint8)
+    return (_c(cat.xq, np.int32), _c(cat.yq, np.int32), _c(cat.g1, np.float32),
+            _c(cat.g2, np.float32), _c(cat.w, np.float32), zb)
+
+
+def moments(s: Setup, cat, centres: Optional[np.ndarray] = None):
+    """G [nc][n_z][n_bins][2n_max+3] and W [nc][n_z][n_bins][2n_max+1], complex128."""
+    xq, yq, g1, g2, w, zb = _cat(cat)
+    if centres is None:
+        centres = np.arange(cat.n, dtype=np.int64)
+    centres = _c(centres, np.int64)
+    nc = centres.shape[0]
+    G = np.zeros((nc, s.n_z, s.n_bins, 2 * s.n_max + 3), dtype=np.complex128)
+    W = np.zeros((nc, s.n_z, s.n_bins, 2 * s.n_max + 1), dtype=np.complex128)
+    cfg = s.c()
+    _check(lib().orc_moments(C.byref(cfg), cat.n, _p(xq), _p(yq), _p(g1), _p(g2), _p(w), _p(zb),
+                             nc, _p(centres), _p(G), _p(W)))
+    return G, W
+
+
+def count_pairs(s: Setup, cat, centres: Optional[np.ndarray] = None) -> int:
+    xq, yq = _c(cat.xq, np.int32), _c(cat.yq, np.int32)
+    if centres is None:
+        centres = np.arange(cat.n, dtype=np.int64)
+    centres = _c(centres, np.int64)
+    out = np.zeros(1, dtype=np.int64)
+    cfg = s.c()
+    _check(lib().orc_count_pairs(C.byref(cfg), cat.n, _p(xq), _p(yq), centres.shape[0],
+                                 _p(centres), _p(out)))
+    return int(out[0])
+
+
+def contract(s: Setup, cat, G, W, centres: Optional[np.ndarray] = None, ups=None, norm=None):
+    """Adds into ups [n_z^3][4][n_max+1][nb][nb] and norm [n_z^3][2n_max+1][nb][nb]."""
+    _, _, g1, g2, w, zb = _cat(cat)
+    if centres is None:
+        centres = np.arange(cat.n, dtype=np.int64)
+    centres = _c(centres, np.int64)
+    z3 = s.n_z ** 3
+    if ups is None:
+        ups = np.zeros((z3, 4, s.n_max + 1, s.n_bins, s.n_bins), dtype=np.complex128)
+    if norm is None:
+        norm = np.zeros((z3, 2 * s.n_max + 1, s.n_bins, s.n_bins), dtype=np.complex128)
+    G = _c(G, np.complex128)
+    W = _c(W, np.complex128)
+    cfg = s.c()
+    _check(lib().orc_contract(C.byref(cfg), _p(g1), _p(g2), _p(w), _p(zb), centres.shape[0],
+                              _p(centres), _p(G), _p(W), _p(ups), _p(norm)))
+    return ups, norm
+
+
+def edge_correct(s: Setup, ups, norm):
+    """Returns (gamma_n [n_z^3][4][2n_max+1][nb][nb], number of singular systems)."""
+    z3 = s.n_z ** 3
+    gam = np.zeros((z3, 4, 2 * s.n_max + 1, s.n_bins, s.n_bins), dtype=np.complex128)
+    ns = np.zeros(1, dtype=np.int64)
+    ups = _c(ups, np.complex128)
+    norm = _c(norm, np.complex128)
+    cfg = s.c()
+    _check(lib().orc_edge_correct(C.byref(cfg), _p(ups), _p(norm), _p(gam), _p(ns)), ok=(0, 5))
+    return gam, int(ns[0])
+
+
+def to_gamma(s: Setup, gam_n, projection: int):
+    z3 = s.n_z ** 3
+    out = np.zeros((z3, 4, s.n_bins, s.n_bins, s.n_phi), dtype=np.complex128)
+    gam_n = _c(gam_n, np.complex128)
+    cfg = s.c()
+    _check(lib().orc_to_gamma(C.byref(cfg), _p(gam_n), projection, _p(out)))
+    return out
+
+
+def to_map3(s: Setup, gamma_cen, theta_ap):
+    """theta_ap: [n_ap][3] arcmin. Returns (corr [n_z^3][n_ap][4] complex, m8 [..][8])."""
+    th = _c(np.atleast_2d(theta_ap), np.float64)
+    n_ap = th.shape[0]
+    z3 = s.n_z ** 3
+    corr = np.zeros((z3, n_ap, 4), dtype=np.complex128)
+    m8 = np.zeros((z3, n_ap, 8))
+    gc = _c(gamma_cen, np.complex128)
+    cfg = s.c()
+    _check(lib().orc_to_map3(C.byref(cfg), _p(gc), n_ap, _p(th), _p(corr), _p(m8)))
+    return corr, m8
+
+
+def filter_F(mu: int, t1: float, t2: float, phi: float, theta) -> complex:
+    th = _c(theta, np.float64)
+    out = np.zeros(2)
+    _check(lib().orc_filter(mu, t1, t2, phi, _p(th), _p(out)))
+    return complex(out[0], out[1])
+
+
+def cen_factor(mu: int, t1: float, t2: float, phi: float) -> complex:
+    out = np.zeros(2)
+    _check(lib().orc_cen_factor(mu, t1, t2, phi, _p(out)))
+    return complex(out[0], out[1])
+
+
+def combine8(corr) -> np.ndarray:
+    c = _c(corr, np.complex128)
+    out = np.zeros(8)
+    _check(lib().orc_combine8(_p(c), _p(out)))
+    return out
+
+
+@dataclass
+class Brute:
+    ups_n: np.ndarray
+    norm_n: np.ndarray
+    ups_b: np.ndarray
+    norm_b: np.ndarray
+    upsc_b: np.ndarray
+    p5_dev: float
+
+
+def brute(s: Setup, cat, n_phib: int = 16) -> Brute:
+    xq, yq, g1, g2, w, zb = _cat(cat)
+    z3 = s.n_z ** 3
+    nb = s.n_bins
+    ups_n = np.zeros((z3, 4, s.n_max + 1, nb, nb), dtype=np.complex128)
+    norm_n = np.zeros((z3, 2 * s.n_max + 1, nb, nb), dtype=np.complex128)
+    ups_b = np.zeros((z3, 4, nb, nb, n_phib), dtype=np.complex128)
+    norm_b = np.zeros((z3, nb, nb, n_phib), dtype=np.complex128)
+    upsc_b = np.zeros((z3, 4, nb, nb, n_phib), dtype=np.complex128)
+    dev = np.zeros(1)
+    cfg = s.c()
+    _check(lib().orc_brute(C.byref(cfg), cat.n, _p(xq), _p(yq), _p(g1), _p(g2), _p(w), _p(zb),
+                           n_phib, _p(ups_n), _p(norm_n), _p(ups_b), _p(norm_b), _p(upsc_b),
+                           _p(dev)))
+    return Brute(ups_n, norm_n, ups_b, norm_b, upsc_b, float(dev[0]))
+
+
+@dataclass
+class Result:
+    G: np.ndarray
+    W: np.ndarray
+    ups: np.ndarray
+    norm: np.ndarray
+    gamma_n: np.ndarray
+    n_singular: int
+    gamma_x: np.ndarray
+    gamma_cen: np.ndarray
+    corr: np.ndarray
+    m8: np.ndarray
+
+
+def pipeline(s: Setup, cat, theta_ap, centres: Optional[np.ndarray] = None) -> Result:
+    """The whole path on the oracle: moments, multipoles, edge correction, Gamma, Map^3."""
+    G, W = moments(s, cat, centres)
+    ups, norm = contract(s, cat, G, W, centres)
+    gam, ns = edge_correct(s, ups, norm)
+    gx = to_gamma(s, gam, 0)
+    gc = to_gamma(s, gam, 1)
+    corr, m8 = to_map3(s, gc, theta_ap)
+    return Result(G, W, ups, norm, gam, ns, gx, gc, corr, m8)
+
+
+__all__ = ["Setup", "build_oracle", "edges", "moments", "count_pairs", "contract",
+           "edge_correct", "to_gamma", "to_map3", "filter_F", "cen_factor", "combine8", "brute",
+           "pipeline", "num_threads", "Result", "Brute"]
