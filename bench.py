@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Benchmark of the multipole shear-3PCF hot path on GB300.
+
+One step = the whole path on one catalog: cell sort, moments (stage a), multipole contraction
+(stage b), edge correction, Gamma^x and Gamma^cen, and the aperture measures. The workload is the
+200k-galaxy lognormal catalog on a 300'x300' patch (20 log bins 0.5'-120', n_max = 30, Map^3 at
+2', 4', 8', 16'). With N GPUs (torchrun) every rank measures its own catalog realisation
+(independent problems, weak scaling, no data-path collective).
+
+Prints one JSON line on rank 0. ``--impl reference`` times the FP64 CPU oracle on a bounded
+centre sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "neighbour-pair harmonic accumulations/s; catalogs/s vs FP64 GPU path at ≤1e-4 Map³ err"
+UNIT = "pair-accumulations/s"
+PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (derived; FP32 FMA pipe)"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
+
+
+def flops_per_pair(n_max: int) -> int:
+    """Algorithmic FP32 flops of stage (a) per neighbour pair in this formulation: unit vector
+    (6), powers z^2..z^{2n_max} (6 per complex product), A_m and B_m for m <= n_max+3 (4 each,
+    real x complex multiply-add), W_m for m <= 2 n_max (4 each)."""
+    return 6 + 6 * (2 * n_max - 1) + 8 * (n_max + 4) + 4 * (2 * n_max + 1)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload_setup(name: str):
+    from paper_2309_08601_gb300 import synth
+    p = synth.WORKLOADS[name]
+    setup = dict(n_bins=p["n_bins"], theta_min=p["theta_min"], theta_max=p["theta_max"],
+                 n_max=p["n_max"])
+    theta = [[t, t, t] for t in p["theta_ap"]]
+    return p, setup, theta
+
+
+def workload_config(name, p, precision):
+    return {"workload": name, "n_galaxies": p["n"], "patch_arcmin": p["side"], "field": p["field"],
+            "n_bins": p["n_bins"], "theta_min_arcmin": p["theta_min"], "theta_max_arcmin": p["theta_max"],
+            "n_max": p["n_max"], "n_phi": 100, "theta_ap_arcmin": p["theta_ap"], "precision": precision,
+            "l2": "inputs (catalog 4 MB) are L2-resident by design; a 256 MiB buffer is written "
+                  "between steps to flush L2", "parallelism": "one catalog per GPU"}
+
+
+# ------------------------------------------------------------------ oracle (CPU) timing
+
+def oracle_sample(cat, setup, theta, target_s: float, seed: int = 0):
+    """Runs the FP64 oracle's whole path on a centre subset sized for about target_s seconds.
+    Returns (pairs, seconds, n_centres, threads)."""
+    import oracle
+    s = oracle.Setup(**setup)
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(cat.n)
+    # calibrate on a few centres, then size the sample
+    probe = np.sort(order[:8])
+    t0 = time.perf_counter()
+    pp = oracle.count_pairs(s, cat, probe)
+    G, W = oracle.moments(s, cat, probe)
+    oracle.contract(s, cat, G, W, probe)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    per_centre = dt / 8
+    k = int(np.clip(target_s / per_centre, 8, cat.n))
+    cen = np.sort(order[:k])
+    pairs = oracle.count_pairs(s, cat, cen)
+    t0 = time.perf_counter()
+    r = oracle.pipeline(s, cat, theta, cen)
+    sec = time.perf_counter() - t0
+    del r, pp
+    return pairs, sec, k, oracle.num_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2309_08601_gb300 import synth
+    oracle.build_oracle()
+    p, setup, theta = workload_setup(args.workload)
+    cat = synth.workload_catalog(args.workload)
+    for _ in range(args.warmup):
+        oracle_sample(cat, setup, theta, target_s=2.0, seed=99)
+    tot_pairs, tot_s, cents = 0, 0.0, 0
+    for k in range(args.steps):
+        pairs, sec, nc, threads = oracle_sample(cat, setup, theta, target_s=args.ref_step_s, seed=k)
+        tot_pairs += pairs
+        tot_s += sec
+        cents += nc
+    value = tot_pairs / tot_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args.workload, p, "fp64-oracle"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "%d random centres per step (all %d galaxies as neighbours), "
+                                       "whole path" % (cents // max(args.steps, 1), cat.n)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2309_08601_gb300 import api, native, synth
+    if rank == 0:
+        from paper_2309_08601_gb300.build import build_native
+        build_native()
+    if dist is not None:
+        dist.barrier()
+    native.lib()
+
+    p, setup, theta = workload_setup(args.workload)
+    cat = synth.make_catalog(p["n"], p["side"], p["seed"] + 1000 * rank, field=p["field"],
+                             weights=p["weights"], holes=p.get("holes", False))
+    dev = api.catalog_to_device(cat)
+    stream = torch.cuda.current_stream()
+    est = api.Estimator(**setup, precision=args.precision, stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        return est.measure(*dev[:5], theta_ap=theta, report_singular=False)
+
+    for _ in range(max(args.warmup, 0)):
+        m = step()
+    torch.cuda.synchronize()
+    n_centres, pairs = est.counts()
+    est.set_timing(True)
+    est.stage_times(reset=True)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        m = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    stages = est.stage_times(reset=True)
+    est.set_timing(False)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    sec = ms_max / 1e3
+    value = world * args.steps * pairs / sec
+    cat_per_s = world * args.steps / sec
+
+    # ---- roofline of the dominant kernel (stage a, FP32 FMA pipe)
+    k1_ms = stages["moments"][0] / args.steps
+    fpp = flops_per_pair(p["n_max"])
+    achieved = fpp * pairs / (k1_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "moments_kernel<float,30>", "achieved": achieved,
+                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": args.k1_traffic, "flops_per_pair": fpp, "pairs_per_launch": pairs,
+                "launch_ms": k1_ms, "peak_source": PEAK_NOTE}
+    launches = sum(v[1] for v in stages.values())
+
+    # ---- end to end through the public API with host buffers
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
+            (cat.xq, cat.yq, cat.g1, cat.g2, cat.w)]
+    h2d = sum(h.numel() * h.element_size() for h in host)
+    out_host = torch.empty((1, len(theta), 8), dtype=torch.float64).pin_memory()
+    d2h = out_host.numel() * out_host.element_size()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        for d, h in zip(dev[:5], host):
+            d.copy_(h, non_blocking=True)
+        m = step()
+        out_host.copy_(m.m8, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_s = float(te.item())
+    e2e = {"value": world * args.steps * pairs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+
+    m8_fp32 = m.m8.cpu().numpy()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64",
+            "data": "synthetic (seeded lognormal Kaiser-Squires shear + shape noise)",
+            "config": workload_config(args.workload, p, args.precision),
+            "catalogs_per_s": cat_per_s, "pairs_per_catalog": pairs,
+            "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks.summary()}
+
+    # ---- the plain FP64 GPU path on the same catalog (rank 0, one untimed-warmup + one run)
+    if rank == 0 and args.fp64_compare:
+        with api.Estimator(**setup, precision="fp64", stream=stream) as e64:
+            sub = torch.zeros(cat.n, dtype=torch.uint8, device="cuda")
+            sub[:64] = 1
+            e64.measure(*dev[:5], theta_ap=theta, centre_mask=sub, report_singular=False)
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            m64 = e64.measure(*dev[:5], theta_ap=theta, report_singular=False)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            s64 = a0.elapsed_time(a1) / 1e3
+            m8_64 = m64.m8.cpu().numpy()
+        err = float(np.abs(m8_fp32[..., 0] - m8_64[..., 0]).max() / np.abs(m8_64[..., 0]).max())
+        err_all = float(np.abs(m8_fp32 - m8_64).max() / np.abs(m8_64).max())
+        line["fp64_path"] = {"catalogs_per_s": 1.0 / s64, "pairs_per_s": pairs / s64,
+                             "speedup_of_measured_path": (cat_per_s / world) * s64,
+                             "map3_rel_err_vs_fp64": err, "m8_rel_err_vs_fp64": err_all}
+
+    if rank == 0 and args.cpu_baseline:
+        pr, sec, k, threads = oracle_sample(cat, setup, theta, target_s=args.cpu_s)
+        line["cpu_baseline"] = {"value": pr / sec, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": "%d random centres (all %d galaxies as neighbours), whole "
+                                          "path, %.1f s" % (k, cat.n, sec)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    est.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="lognormal_200k")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work sampled")
+    ap.add_argument("--ref-step-s", type=float, default=8.0)
+    ap.add_argument("--k1-traffic", type=float, default=None,
+                    help="DRAM bytes per moments launch from the committed ncu summary")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

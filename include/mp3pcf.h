@@ -1,0 +1,164 @@
+/*
+ * mp3pcf — GB300 (sm_103a) library for the multipole estimator of the shear three-point
+ * correlation function of Porth et al. (2023), "Efficient estimation of third-order shear
+ * correlation functions".
+ *
+ * C ABI. All pointers named d_* are DEVICE pointers owned by the caller; all pointers named
+ * h_* are HOST pointers owned by the caller. The context owns only its own workspace. Every
+ * call is stream-ordered on the stream given to mp3pcf_create and returns a status code; no
+ * call throws. Calls that must return a count to the host (noted below) synchronise the stream.
+ * One context must not be used from two host threads at the same time.
+ *
+ * Complex numbers are interleaved (re, im). Floating-point outputs of the multipole stages are
+ * always FP64; the moments are FP32 or FP64 as the precision setting says.
+ *
+ * Conventions (Sec. 2 and Sec. 3 of the paper):
+ *   gamma_c = gamma_1 + i gamma_2; a galaxy's contribution carries v = w gamma_c;
+ *   radial bins are logarithmic, e_b = theta_min (theta_max/theta_min)^(b/n_bins), b = 0..n_bins,
+ *   and a pair is in bin b iff e_b <= separation < e_{b+1}; the test is exact, on the integer
+ *   squared separation of the fixed-point positions against ceil((e_b/quantum)^2);
+ *   Z-triplet index zt = (Z1*n_z + Z2)*n_z + Z3 (centre galaxy in Z1, the galaxy at the first
+ *   radial bin in Z2, the one at the second radial bin in Z3), Eq. tomoGn.
+ */
+#ifndef MP3PCF_H
+#define MP3PCF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MP3PCF_OK = 0,
+    MP3PCF_EINVAL = 1,      /* bad argument or configuration */
+    MP3PCF_ENOMEM = 2,      /* device workspace could not be allocated */
+    MP3PCF_ECUDA = 3,       /* a CUDA runtime call failed; see mp3pcf_last_error */
+    MP3PCF_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
+    MP3PCF_ESINGULAR = 5,   /* at least one mode-coupling system was singular (N_0 = 0) */
+    MP3PCF_EUNSUPPORTED = 6 /* valid request this build does not implement */
+} mp3pcf_status;
+
+typedef enum {
+    MP3PCF_FP64 = 0,        /* moments and contraction in FP64 */
+    MP3PCF_FP32 = 1,        /* moments in FP32, contraction FP32 with FP64 tile sums */
+    MP3PCF_FP32_BF16X3 = 2, /* moments in FP32, contraction on tensor cores, BF16 hi+lo split */
+    MP3PCF_FP32_TF32X3 = 3  /* moments in FP32, contraction on tensor cores, TF32 hi+lo split */
+} mp3pcf_precision;
+
+typedef struct {
+    int32_t n_bins;        /* number of logarithmic radial bins, >= 1 */
+    double theta_min;      /* inner edge of the first bin, arcmin, > 0 */
+    double theta_max;      /* outer edge of the last bin, arcmin, > theta_min */
+    int32_t n_max;         /* largest multipole order, 0 <= n_max <= 50 */
+    int32_t n_phi;         /* angular grid of to_gamma/to_map3, phi_k = (k+1/2) 2 pi/n_phi */
+    int32_t n_z;           /* tomographic bins, 1..8 (1 = no tomography) */
+    double quantum;        /* arcmin per unit of the int32 fixed-point positions, > 0 */
+    int32_t precision;     /* mp3pcf_precision */
+    int32_t norm_truncate; /* 1: drop N_m with |m| > n_max from the coupling matrix */
+    int32_t radial_nodes;  /* 0: bin node (e_b+e_{b+1})/2, 1: sqrt(e_b e_{b+1}) */
+    int32_t reserved[5];   /* must be zero */
+} mp3pcf_config;
+
+typedef struct mp3pcf_ctx mp3pcf_ctx;
+
+/* Validates cfg, binds the current CUDA device and the given stream (cudaStream_t, may be
+ * NULL for the legacy default stream), and creates a context. On success *out owns the context;
+ * release it with mp3pcf_destroy. EINVAL on a bad configuration (nothing is allocated). */
+mp3pcf_status mp3pcf_create(const mp3pcf_config* cfg, void* stream, mp3pcf_ctx** out);
+
+/* Frees the context and its workspace (synchronises its stream). NULL is accepted. */
+mp3pcf_status mp3pcf_destroy(mp3pcf_ctx* ctx);
+
+/* Text of the last error on this context (never NULL; empty if none). */
+const char* mp3pcf_last_error(const mp3pcf_ctx* ctx);
+
+/* Host-only, no CUDA call: the bin edges e_b (arcmin, n_bins+1 values) and the exact integer
+ * squared edges ceil((e_b/quantum)^2) (n_bins+1 values) the pair test uses (Sec. 2.3; the
+ * half-open reading of the bin interval). Either output may be NULL. */
+mp3pcf_status mp3pcf_bin_edges(const mp3pcf_config* cfg, double* h_edges, int64_t* h_edges2_q);
+
+/* Stage (a), Eq. Gn_disc and the W_n of Eq. 3PCF_Normalization, Sec. 3.1. For every selected
+ * centre galaxy i, radial bin b and neighbour bin Z:
+ *   G_m(i,b,Z) = sum_k w_k gamma_c,k e^{i m varphi_ik} [theta_ik in bin b, zbin_k = Z],
+ *                m = -n_max-3 .. n_max-1,
+ *   W_m(i,b,Z) = sum_k w_k e^{i m varphi_ik} [...],  m = 0 .. 2 n_max,
+ * over all n galaxies k as neighbours. Inputs (device, n entries each): d_xq, d_yq int32
+ * fixed-point positions (units of cfg.quantum; differences must fit in int32), d_g1, d_g2, d_w
+ * float32 (w >= 0), d_zbin uint8 in [0, n_z) or NULL (all bin 0), d_centre_mask uint8 or NULL
+ * (NULL: every galaxy is a centre; else galaxy i is a centre iff mask[i] != 0). The catalog is
+ * cell-sorted into the context's workspace; results stay in the context (read them with
+ * mp3pcf_copy_moments, contract them with mp3pcf_contract_multipoles). n = 0 is allowed.
+ * Synchronises the stream once (grid extent and centre count). */
+mp3pcf_status mp3pcf_accumulate_moments(mp3pcf_ctx* ctx, int64_t n, const int32_t* d_xq,
+                                        const int32_t* d_yq, const float* d_g1, const float* d_g2,
+                                        const float* d_w, const uint8_t* d_zbin,
+                                        const uint8_t* d_centre_mask);
+
+/* Number of centres of the last accumulate call and the number of ordered (centre, neighbour)
+ * pairs it accumulated (host outputs, either may be NULL). Synchronises the stream. */
+mp3pcf_status mp3pcf_counts(mp3pcf_ctx* ctx, int64_t* h_n_centres, int64_t* h_n_pairs);
+
+/* Copies the moments of the last accumulate call to caller device buffers, centres in
+ * increasing galaxy index: d_G [n_centres][n_z][n_bins][2 n_max + 3] (m = -n_max-3..n_max-1),
+ * d_W [n_centres][n_z][n_bins][2 n_max + 1] (m = 0..2 n_max), complex float for the FP32 modes
+ * and complex double for MP3PCF_FP64. Either pointer may be NULL. */
+mp3pcf_status mp3pcf_copy_moments(mp3pcf_ctx* ctx, void* d_G, void* d_W);
+
+/* Stage (b), Eqs. Upsilon0_Derivation, Upsilon1-3, 3PCF_Normalization and tomoGn, Sec. 3.1:
+ *   Upsilon_0,n = - sum_i v_i   G_{n-3}(b1) G_{-n-3}(b2)
+ *   Upsilon_1,n = - sum_i v_i^* G_{n-1}(b1) G_{-n-1}(b2)
+ *   Upsilon_2,n = - sum_i v_i   G_{-n-1}(b1)^* G_{-n-3}(b2)
+ *   Upsilon_3,n = - sum_i v_i   G_{n-3}(b1) G_{n-1}(b2)^*
+ *   N_n         =   sum_i w_i   W_n(b1) W_n(b2)^*
+ * summed over the centres of the last accumulate call and ADDED to d_upsilon
+ * [n_z^3][4][n_max+1][n_bins][n_bins] (n = 0..n_max) and d_norm [n_z^3][2 n_max+1][n_bins][n_bins]
+ * (n = 0..2 n_max), complex double. Adding lets callers sum centre chunks or patches
+ * (App. B, Eq. PatchGamma). */
+mp3pcf_status mp3pcf_contract_multipoles(mp3pcf_ctx* ctx, double* d_upsilon, double* d_norm);
+
+/* Edge correction, Eqs. ModeCoupling and GammaMultipolesWithEC, Sec. 3.4: per (zt, b1, b2)
+ * solves sum_n N_{l-n} Gamma_{mu,n} = Upsilon_{mu,l}, l, n in [-n_max, n_max], in FP64 with
+ * partial pivoting. Negative orders come from the symmetries of App. A
+ * (Upsilon_{0,-n}(i,j) = Upsilon_{0,n}(j,i), Upsilon_{1,-n}(i,j) = Upsilon_{1,n}(j,i),
+ * Upsilon_{2,-n}(i,j) = Upsilon_{3,n}(j,i), N_{-n}(i,j) = N_n(j,i), with Z2 <-> Z3).
+ * Output d_gamma_n [n_z^3][4][2 n_max+1][n_bins][n_bins] complex double, n = -n_max..n_max;
+ * Gamma(phi) = sum_n Gamma_n e^{i n phi} (no 1/2pi, the normalisation Eq. ModeCoupling
+ * implies). Systems with N_0 = 0 or a zero pivot get NaN and the call returns ESINGULAR with
+ * their number in *h_n_singular (host, may be NULL; a non-NULL pointer synchronises). */
+mp3pcf_status mp3pcf_edge_correct(mp3pcf_ctx* ctx, const double* d_upsilon, const double* d_norm,
+                                  double* d_gamma_n, int64_t* h_n_singular);
+
+/* Gamma^x_mu(b1, b2, phi_k) = sum_n Gamma_{mu,n} e^{i n phi_k}, phi_k = (k+1/2) 2 pi / n_phi
+ * (Sec. 4: linear angular bins on [0, 2 pi]); projection 1 multiplies by the rotation factors
+ * of Eqs. X2Centroid0-3 (Sec. 2.2) evaluated at the radial nodes of b1 and b2, giving the
+ * centroid projection. Output d_gamma_phi [n_z^3][4][n_bins][n_bins][n_phi] complex double. */
+mp3pcf_status mp3pcf_to_gamma(mp3pcf_ctx* ctx, const double* d_gamma_n, int32_t projection,
+                              double* d_gamma_phi);
+
+/* Third-order aperture measures, Eqs. MFrom3pcfTheory, MFrom3pcfTheoryb (Sec. 5.2) with the
+ * Q filter of Eq. CrittendenQ and the filters of App. C, by the midpoint rule over the radial
+ * bins and the n_phi angular nodes:
+ *   corr_mu = sum_{b1,b2,k} Gamma^cen_mu(b1,b2,phi_k) F_mu(t_b1, t_b2, phi_k) dt_b1 dt_b2 dphi.
+ * d_gamma_cen: output of mp3pcf_to_gamma with projection 1. d_theta_ap [n_ap][3] aperture radii
+ * (arcmin, device). Outputs (device): d_corr [n_z^3][n_ap][4] complex double
+ * (<M^3>, <M^* M^2>, <M M^* M>, <M^2 M^*>) and d_m8 [n_z^3][n_ap][8] double, the eight real
+ * measures of Eqs. MapTrafo8_1-8 in the order Map^3, <Mx Map Map>, <Map Mx Map>,
+ * <Map Map Mx>, <Map Mx Mx>, <Mx Map Mx>, <Mx Mx Map>, Mx^3. Either output may be NULL. */
+mp3pcf_status mp3pcf_to_map3(mp3pcf_ctx* ctx, const double* d_gamma_cen, int64_t n_ap,
+                             const double* d_theta_ap, double* d_corr, double* d_m8);
+
+/* Tracing. With timing on, every stage call records a pair of CUDA events on the context
+ * stream around its kernels. mp3pcf_stage_times returns, per stage, the accumulated device time
+ * in ms (h_ms[6], may be NULL) and the number of kernel launches (h_launches[6], may be NULL;
+ * counted whether or not timing is on) since the last reset. Stages: 0 cell sort (step a0),
+ * 1 moments (a1), 2 contraction (b1), 3 edge correction (c1), 4 to_gamma (c2), 5 to_map3 (c3).
+ * reset != 0 clears the counters after reading. Synchronises the stream. */
+mp3pcf_status mp3pcf_set_timing(mp3pcf_ctx* ctx, int32_t on);
+mp3pcf_status mp3pcf_stage_times(mp3pcf_ctx* ctx, double* h_ms, int64_t* h_launches, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MP3PCF_H */

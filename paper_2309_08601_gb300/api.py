@@ -1,0 +1,229 @@
+"""Torch-facing wrapper of the mp3pcf C ABI.
+
+PyTorch provides device memory and the CUDA stream; every step of the estimator runs in the
+library's CUDA kernels. Tensors passed in must be contiguous CUDA tensors of the documented
+dtypes; outputs are allocated with torch on the estimator's device.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from . import native
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("mp3pcf needs a CUDA device; there is no CPU fallback")
+    return torch
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _need(t, dtype, name, n=None):
+    torch = _torch()
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if n is not None and t.numel() != n:
+        raise ValueError("%s must have %d entries" % (name, n))
+    return t
+
+
+@dataclass
+class Measurement:
+    upsilon: object  # [n_z^3][4][n_max+1][nb][nb] complex128
+    norm: object     # [n_z^3][2n_max+1][nb][nb] complex128
+    gamma_n: object  # [n_z^3][4][2n_max+1][nb][nb] complex128
+    n_singular: int
+    gamma_x: object    # [n_z^3][4][nb][nb][n_phi]
+    gamma_cen: object  # [n_z^3][4][nb][nb][n_phi]
+    corr: object       # [n_z^3][n_ap][4] complex128
+    m8: object         # [n_z^3][n_ap][8] float64
+
+
+class Estimator:
+    """One library context: a measurement setup bound to a device and a stream."""
+
+    def __init__(self, n_bins, theta_min, theta_max, n_max, *, n_phi=100, n_z=1,
+                 quantum=2.0 ** -13, precision="fp32", norm_truncate=False,
+                 radial_nodes="arithmetic", stream=None):
+        torch = _torch()
+        self.cfg = native.make_config(n_bins, theta_min, theta_max, n_max, n_phi, n_z, quantum,
+                                      precision, norm_truncate, radial_nodes)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.precision = precision
+        self._ctx = C.c_void_p()
+        native.check(native.lib().mp3pcf_create(C.byref(self.cfg), C.c_void_p(self.stream.cuda_stream),
+                                                C.byref(self._ctx)), "mp3pcf_create")
+
+    # ------------------------------------------------------------------ lifetime
+    def close(self):
+        if self._ctx:
+            native.lib().mp3pcf_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------------ shapes
+    @property
+    def n_bins(self):
+        return self.cfg.n_bins
+
+    @property
+    def n_max(self):
+        return self.cfg.n_max
+
+    @property
+    def n_z(self):
+        return self.cfg.n_z
+
+    @property
+    def z3(self):
+        return self.cfg.n_z ** 3
+
+    def bin_edges(self):
+        e = np.zeros(self.n_bins + 1)
+        e2 = np.zeros(self.n_bins + 1, dtype=np.int64)
+        native.check(native.lib().mp3pcf_bin_edges(C.byref(self.cfg), e.ctypes.data_as(C.c_void_p),
+                                                   e2.ctypes.data_as(C.c_void_p)), "mp3pcf_bin_edges")
+        return e, e2
+
+    # ------------------------------------------------------------------ stage (a)
+    def accumulate_moments(self, xq, yq, g1, g2, w, zbin=None, centre_mask=None):
+        torch = _torch()
+        n = int(xq.numel())
+        _need(xq, torch.int32, "xq", n)
+        _need(yq, torch.int32, "yq", n)
+        _need(g1, torch.float32, "g1", n)
+        _need(g2, torch.float32, "g2", n)
+        _need(w, torch.float32, "w", n)
+        _need(zbin, torch.uint8, "zbin", n)
+        _need(centre_mask, torch.uint8, "centre_mask", n)
+        st = native.lib().mp3pcf_accumulate_moments(self._ctx, n, _ptr(xq), _ptr(yq), _ptr(g1),
+                                                    _ptr(g2), _ptr(w), _ptr(zbin), _ptr(centre_mask))
+        native.check(st, "mp3pcf_accumulate_moments", self._ctx)
+
+    def counts(self):
+        nc = C.c_int64()
+        npairs = C.c_int64()
+        native.check(native.lib().mp3pcf_counts(self._ctx, C.byref(nc), C.byref(npairs)),
+                     "mp3pcf_counts", self._ctx)
+        return nc.value, npairs.value
+
+    def moments(self):
+        torch = _torch()
+        nc, _ = self.counts()
+        dt = torch.complex128 if self.precision == "fp64" else torch.complex64
+        G = torch.empty((nc, self.n_z, self.n_bins, 2 * self.n_max + 3), dtype=dt, device=self.device)
+        W = torch.empty((nc, self.n_z, self.n_bins, 2 * self.n_max + 1), dtype=dt, device=self.device)
+        native.check(native.lib().mp3pcf_copy_moments(self._ctx, _ptr(G), _ptr(W)),
+                     "mp3pcf_copy_moments", self._ctx)
+        return G, W
+
+    # ------------------------------------------------------------------ stage (b)
+    def new_multipoles(self):
+        torch = _torch()
+        ups = torch.zeros((self.z3, 4, self.n_max + 1, self.n_bins, self.n_bins),
+                          dtype=torch.complex128, device=self.device)
+        norm = torch.zeros((self.z3, 2 * self.n_max + 1, self.n_bins, self.n_bins),
+                           dtype=torch.complex128, device=self.device)
+        return ups, norm
+
+    def contract(self, ups=None, norm=None):
+        """Adds this catalog's multipoles into (ups, norm) (fresh zero buffers if None)."""
+        if ups is None or norm is None:
+            ups, norm = self.new_multipoles()
+        native.check(native.lib().mp3pcf_contract_multipoles(self._ctx, _ptr(ups), _ptr(norm)),
+                     "mp3pcf_contract_multipoles", self._ctx)
+        return ups, norm
+
+    # ------------------------------------------------------------------ FP64 post-processing
+    def edge_correct(self, ups, norm, report_singular=True):
+        torch = _torch()
+        gam = torch.empty((self.z3, 4, 2 * self.n_max + 1, self.n_bins, self.n_bins),
+                          dtype=torch.complex128, device=self.device)
+        ns = C.c_int64(0)
+        st = native.lib().mp3pcf_edge_correct(self._ctx, _ptr(ups), _ptr(norm), _ptr(gam),
+                                              C.byref(ns) if report_singular else None)
+        native.check(st, "mp3pcf_edge_correct", self._ctx, ok=(native.OK, native.ESINGULAR))
+        return gam, int(ns.value)
+
+    def to_gamma(self, gamma_n, projection: int):
+        torch = _torch()
+        out = torch.empty((self.z3, 4, self.n_bins, self.n_bins, self.cfg.n_phi),
+                          dtype=torch.complex128, device=self.device)
+        native.check(native.lib().mp3pcf_to_gamma(self._ctx, _ptr(gamma_n), int(projection), _ptr(out)),
+                     "mp3pcf_to_gamma", self._ctx)
+        return out
+
+    def to_map3(self, gamma_cen, theta_ap):
+        torch = _torch()
+        th = torch.as_tensor(np.atleast_2d(np.asarray(theta_ap, dtype=np.float64)),
+                             device=self.device).contiguous()
+        n_ap = th.shape[0]
+        corr = torch.empty((self.z3, n_ap, 4), dtype=torch.complex128, device=self.device)
+        m8 = torch.empty((self.z3, n_ap, 8), dtype=torch.float64, device=self.device)
+        native.check(native.lib().mp3pcf_to_map3(self._ctx, _ptr(gamma_cen), n_ap, _ptr(th),
+                                                 _ptr(corr), _ptr(m8)), "mp3pcf_to_map3", self._ctx)
+        return corr, m8
+
+    # ------------------------------------------------------------------ tracing
+    STAGES = ("sort", "moments", "contract", "edge_correct", "to_gamma", "to_map3")
+
+    def set_timing(self, on: bool = True):
+        native.check(native.lib().mp3pcf_set_timing(self._ctx, int(bool(on))), "mp3pcf_set_timing")
+
+    def stage_times(self, reset: bool = True):
+        """{stage: (device ms, kernel launches)} since the last reset (synchronises)."""
+        ms = np.zeros(6)
+        nl = np.zeros(6, dtype=np.int64)
+        native.check(native.lib().mp3pcf_stage_times(self._ctx, ms.ctypes.data_as(C.c_void_p),
+                                                     nl.ctypes.data_as(C.c_void_p), int(reset)),
+                     "mp3pcf_stage_times", self._ctx)
+        return {k: (float(ms[i]), int(nl[i])) for i, k in enumerate(self.STAGES)}
+
+    # ------------------------------------------------------------------ whole path
+    def measure(self, xq, yq, g1, g2, w, theta_ap, zbin=None, centre_mask=None,
+                report_singular=True) -> Measurement:
+        self.accumulate_moments(xq, yq, g1, g2, w, zbin, centre_mask)
+        ups, norm = self.contract()
+        gam, ns = self.edge_correct(ups, norm, report_singular)
+        gx = self.to_gamma(gam, 0)
+        gc = self.to_gamma(gam, 1)
+        corr, m8 = self.to_map3(gc, theta_ap)
+        return Measurement(ups, norm, gam, ns, gx, gc, corr, m8)
+
+
+def catalog_to_device(cat, device=None):
+    """Copies a synth.Catalog to CUDA tensors (xq, yq, g1, g2, w, zbin-or-None)."""
+    torch = _torch()
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    zb = None if cat.zbin is None else torch.as_tensor(np.ascontiguousarray(cat.zbin, np.uint8), device=dev)
+    return (torch.as_tensor(np.ascontiguousarray(cat.xq, np.int32), device=dev),
+            torch.as_tensor(np.ascontiguousarray(cat.yq, np.int32), device=dev),
+            torch.as_tensor(np.ascontiguousarray(cat.g1, np.float32), device=dev),
+            torch.as_tensor(np.ascontiguousarray(cat.g2, np.float32), device=dev),
+            torch.as_tensor(np.ascontiguousarray(cat.w, np.float32), device=dev), zb)

@@ -1,0 +1,811 @@
+// C ABI of the mp3pcf library and the cell sort (step a0): fixed-point catalog -> galaxies
+// ordered by (tomographic bin, cell row, cell column, galaxy index), with cell start offsets.
+#include <cuda_runtime.h>
+#include <limits.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace mp3 {
+
+// ------------------------------------------------------------------ device buffers
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes)
+    {
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = bytes < 256 ? 256 : bytes;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) cap = want;
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <typename U>
+    U* as() const
+    {
+        return reinterpret_cast<U*>(p);
+    }
+};
+
+// ------------------------------------------------------------------ a0: cell sort kernels
+
+__global__ void k_bbox_init(int* bb)
+{
+    bb[0] = INT_MAX;
+    bb[1] = INT_MAX;
+    bb[2] = INT_MIN;
+    bb[3] = INT_MIN;
+    bb[4] = 0;  // error flags
+}
+
+__global__ void k_bbox(int64_t n, const int32_t* __restrict__ xq, const int32_t* __restrict__ yq,
+                       const uint8_t* __restrict__ zb, int nz, int* bb)
+{
+    int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN, bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = xq[i], y = yq[i];
+        mnx = min(mnx, x);
+        mny = min(mny, y);
+        mxx = max(mxx, x);
+        mxy = max(mxy, y);
+        if (zb && zb[i] >= nz) bad = 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mnx = min(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+        mny = min(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+        mxx = max(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+        mxy = max(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&bb[0], mnx);
+        atomicMin(&bb[1], mny);
+        atomicMax(&bb[2], mxx);
+        atomicMax(&bb[3], mxy);
+        if (bad) atomicOr(&bb[4], 1);
+    }
+}
+
+__global__ void k_keys(int64_t n, const int32_t* __restrict__ xq, const int32_t* __restrict__ yq,
+                       const uint8_t* __restrict__ zb, GridDesc g, int* __restrict__ key,
+                       int* __restrict__ count)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int cx_ = (int)(((long long)xq[i] - g.x0) / g.side);
+        const int cy_ = (int)(((long long)yq[i] - g.y0) / g.side);
+        const int k = (zb ? (int)zb[i] : 0) * g.ncells + cy_ * g.ncx + cx_;
+        key[i] = k;
+        atomicAdd(&count[k], 1);
+    }
+}
+
+// exclusive scan in three passes (block scan, scan of block sums, add), deterministic
+constexpr int kScanBlock = 1024;
+
+__global__ void k_scan_blocks(const int* __restrict__ in, int* __restrict__ out, int64_t K,
+                              int* __restrict__ sums)
+{
+    __shared__ int wsum[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+    const int t = threadIdx.x;  // 256 threads x 4 elements
+    int v[4];
+    int run = 0;
+    for (int q = 0; q < 4; ++q) {
+        const int64_t i = base + t * 4 + q;
+        v[q] = i < K ? in[i] : 0;
+        run += v[q];
+    }
+    // warp inclusive scan of per-thread totals
+    int x = run;
+    const int lane = t & 31, wid = t >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int s = lane < 8 ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < 8) wsum[lane] = s;
+    }
+    __syncthreads();
+    int excl = x - run + (wid > 0 ? wsum[wid - 1] : 0);
+    for (int q = 0; q < 4; ++q) {
+        const int64_t i = base + t * 4 + q;
+        if (i < K) out[i] = excl;
+        excl += v[q];
+    }
+    if (t == 255) sums[blockIdx.x] = excl;
+}
+
+__global__ void k_scan_sums(int* sums, int nblocks, int* total)
+{
+    // one block of 1024 threads, sequential over tiles of 1024 sums
+    __shared__ int wsum[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int b0 = 0; b0 < nblocks; b0 += 1024) {
+        const int i = b0 + threadIdx.x;
+        const int v = i < nblocks ? sums[i] : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int s = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            wsum[lane] = s;
+        }
+        __syncthreads();
+        const int incl = x + (wid > 0 ? wsum[wid - 1] : 0);
+        if (i < nblocks) sums[i] = carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_add(int* __restrict__ out, int64_t K, const int* __restrict__ sums)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+    const int add = sums[blockIdx.x];
+    for (int q = threadIdx.x; q < kScanBlock; q += blockDim.x) {
+        const int64_t i = base + q;
+        if (i < K) out[i] += add;
+    }
+}
+
+__global__ void k_scatter(int64_t n, const int* __restrict__ key, const int* __restrict__ start,
+                          int* __restrict__ fill, int* __restrict__ perm)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int k = key[i];
+        perm[start[k] + atomicAdd(&fill[k], 1)] = (int)i;
+    }
+}
+
+// atomics leave the order inside a cell arbitrary; restore increasing galaxy index so that the
+// whole pipeline is deterministic
+__global__ void k_cell_order(int64_t K, const int* __restrict__ start, int* __restrict__ perm)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < K;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int a = start[c], b = start[c + 1];
+        for (int i = a + 1; i < b; ++i) {
+            const int v = perm[i];
+            int j = i - 1;
+            while (j >= a && perm[j] > v) {
+                perm[j + 1] = perm[j];
+                --j;
+            }
+            perm[j + 1] = v;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_gather(int64_t n, const int* __restrict__ perm, const int32_t* __restrict__ xq,
+                         const int32_t* __restrict__ yq, const float* __restrict__ g1,
+                         const float* __restrict__ g2, const float* __restrict__ w,
+                         const uint8_t* __restrict__ zb, const uint8_t* __restrict__ mask,
+                         int2* __restrict__ pos, T* __restrict__ pa, T* __restrict__ pb,
+                         T* __restrict__ pw, uint8_t* __restrict__ zs, int* __restrict__ cflag)
+{
+    for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < n;
+         d += (int64_t)gridDim.x * blockDim.x) {
+        const int i = perm[d];
+        pos[d] = make_int2(xq[i], yq[i]);
+        const T wi = (T)w[i];
+        pa[d] = wi * (T)g1[i];
+        pb[d] = wi * (T)g2[i];
+        pw[d] = wi;
+        zs[d] = zb ? zb[i] : 0;
+        cflag[d] = mask ? (mask[i] != 0) : 1;
+    }
+}
+
+__global__ void k_mask_flags(int64_t n, const uint8_t* __restrict__ mask, int* __restrict__ f)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        f[i] = mask ? (mask[i] != 0) : 1;
+}
+
+// centre list in sorted order and, for each centre, its row in galaxy-index order
+__global__ void k_centres(int64_t n, const int* __restrict__ perm, const int* __restrict__ cflag,
+                          const int* __restrict__ crank, const int* __restrict__ orank,
+                          int* __restrict__ centre_idx, int* __restrict__ crow)
+{
+    for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < n;
+         d += (int64_t)gridDim.x * blockDim.x) {
+        if (cflag[d]) {
+            const int r = crank[d];
+            centre_idx[r] = (int)d;
+            crow[r] = orank[perm[d]];
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_copy_rows(int64_t rows, int row_len, const int* __restrict__ crow,
+                            const cx<T>* __restrict__ src, cx<T>* __restrict__ dst)
+{
+    // src row r (sorted centre order) -> dst row crow[r]
+    const int64_t total = rows * row_len;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / row_len, q = t % row_len;
+        dst[(int64_t)crow[r] * row_len + q] = src[t];
+    }
+}
+
+}  // namespace mp3
+
+using namespace mp3;
+
+// ------------------------------------------------------------------ context
+
+struct mp3pcf_ctx {
+    mp3pcf_config cfg;
+    cudaStream_t st = nullptr;
+    int device = 0;
+    int n_sm = 0;
+    bool fp64 = false;
+    std::vector<double> edges, nodes;
+    std::vector<long long> e2q;
+    std::string err;
+    // catalog state of the last accumulate call
+    int64_t n = 0;
+    int64_t n_centres = 0;
+    GridDesc grid{};
+    DevBuf d_e2q, d_edges, d_nodes;
+    DevBuf bb, key, count, fill, scan_sums, scan_total, perm, pos, pa, pb, pw, zs;
+    DevBuf cflag, crank, oflag, orank, centre_idx, crow;
+    DevBuf G, W, pairs, partial, singular, m3partial;
+    // tracing: per-stage event pairs and kernel-launch counts
+    bool timing = false;
+    int64_t launches[6] = {0, 0, 0, 0, 0, 0};
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+    std::vector<cudaEvent_t> pool;
+};
+
+enum { ST_SORT = 0, ST_MOMENTS = 1, ST_CONTRACT = 2, ST_EDGE = 3, ST_GAMMA = 4, ST_MAP3 = 5 };
+
+static cudaEvent_t stage_begin(mp3pcf_ctx* ctx)
+{
+    if (!ctx->timing) return nullptr;
+    cudaEvent_t e = nullptr;
+    if (!ctx->pool.empty()) {
+        e = ctx->pool.back();
+        ctx->pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        return nullptr;
+    }
+    cudaEventRecord(e, ctx->st);
+    return e;
+}
+
+static void stage_end(mp3pcf_ctx* ctx, int stage, cudaEvent_t b)
+{
+    if (!b) return;
+    cudaEvent_t e = stage_begin(ctx);
+    if (!e) {
+        ctx->pool.push_back(b);
+        return;
+    }
+    ctx->ev.push_back({stage, {b, e}});
+}
+
+// records the end event of a stage when it goes out of scope
+struct StageScope {
+    mp3pcf_ctx* ctx;
+    int stage;
+    cudaEvent_t b;
+    StageScope(mp3pcf_ctx* c, int s) : ctx(c), stage(s), b(stage_begin(c)) {}
+    ~StageScope() { stage_end(ctx, stage, b); }
+};
+
+static mp3pcf_status fail(mp3pcf_ctx* c, mp3pcf_status s, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+#define MP3_CK(call)                                                                       \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? MP3PCF_ENOMEM : MP3PCF_ECUDA, \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));               \
+    } while (0)
+
+static bool config_valid(const mp3pcf_config* c, std::string* why)
+{
+    auto bad = [&](const char* m) {
+        if (why) *why = m;
+        return false;
+    };
+    if (!c) return bad("null config");
+    if (c->n_bins < 1 || c->n_bins > kMaxBins) return bad("n_bins out of range");
+    if (!(c->theta_min > 0) || !(c->theta_max > c->theta_min) || !std::isfinite(c->theta_max))
+        return bad("need 0 < theta_min < theta_max");
+    if (c->n_max < 0 || c->n_max > kMaxNmax) return bad("n_max out of range");
+    if (c->n_phi < 1 || c->n_phi > 100000) return bad("n_phi out of range");
+    if (c->n_z < 1 || c->n_z > kMaxNz) return bad("n_z out of range");
+    if (!(c->quantum > 0) || !std::isfinite(c->quantum)) return bad("quantum must be > 0");
+    if (c->precision < MP3PCF_FP64 || c->precision > MP3PCF_FP32_TF32X3) return bad("precision");
+    if (c->norm_truncate != 0 && c->norm_truncate != 1) return bad("norm_truncate");
+    if (c->radial_nodes != 0 && c->radial_nodes != 1) return bad("radial_nodes");
+    for (int r : c->reserved)
+        if (r != 0) return bad("reserved fields must be zero");
+    const double t = c->theta_max / c->quantum;
+    if (t * t >= 9.0e18) return bad("theta_max / quantum too large");
+    return true;
+}
+
+// bin edges and their exact squared fixed-point values (same definition the header states)
+static void host_edges(const mp3pcf_config* c, std::vector<double>& e, std::vector<long long>& e2)
+{
+    e.resize(c->n_bins + 1);
+    e2.resize(c->n_bins + 1);
+    for (int b = 0; b <= c->n_bins; ++b) {
+        const double eb = c->theta_min * pow(c->theta_max / c->theta_min, (double)b / c->n_bins);
+        const double t = eb / c->quantum;
+        e[b] = eb;
+        e2[b] = (long long)ceil(t * t);
+    }
+}
+
+extern "C" {
+
+mp3pcf_status mp3pcf_bin_edges(const mp3pcf_config* cfg, double* h_edges, int64_t* h_edges2_q)
+{
+    if (!config_valid(cfg, nullptr)) return MP3PCF_EINVAL;
+    std::vector<double> e;
+    std::vector<long long> e2;
+    host_edges(cfg, e, e2);
+    for (int b = 0; b <= cfg->n_bins; ++b) {
+        if (h_edges) h_edges[b] = e[b];
+        if (h_edges2_q) h_edges2_q[b] = (int64_t)e2[b];
+    }
+    return MP3PCF_OK;
+}
+
+mp3pcf_status mp3pcf_create(const mp3pcf_config* cfg, void* stream, mp3pcf_ctx** out)
+{
+    if (!out) return MP3PCF_EINVAL;
+    *out = nullptr;
+    std::string why;
+    if (!config_valid(cfg, &why)) return MP3PCF_EINVAL;
+    mp3pcf_ctx* ctx = new mp3pcf_ctx();
+    ctx->cfg = *cfg;
+    ctx->st = (cudaStream_t)stream;
+    ctx->fp64 = cfg->precision == MP3PCF_FP64;
+    host_edges(cfg, ctx->edges, ctx->e2q);
+    ctx->nodes.resize(cfg->n_bins);
+    for (int b = 0; b < cfg->n_bins; ++b)
+        ctx->nodes[b] = cfg->radial_nodes ? sqrt(ctx->edges[b] * ctx->edges[b + 1])
+                                          : 0.5 * (ctx->edges[b] + ctx->edges[b + 1]);
+    auto cleanup = [&](mp3pcf_status s) {
+        mp3pcf_destroy(ctx);
+        return s;
+    };
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) return cleanup(MP3PCF_ECUDA);
+    if (cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess)
+        return cleanup(MP3PCF_ECUDA);
+    const int nb = cfg->n_bins;
+    if (ctx->d_e2q.ensure(sizeof(long long) * (nb + 1)) != cudaSuccess ||
+        ctx->d_edges.ensure(sizeof(double) * (nb + 1)) != cudaSuccess ||
+        ctx->d_nodes.ensure(sizeof(double) * nb) != cudaSuccess ||
+        ctx->bb.ensure(sizeof(int) * 8) != cudaSuccess || ctx->pairs.ensure(8) != cudaSuccess ||
+        ctx->singular.ensure(8) != cudaSuccess)
+        return cleanup(MP3PCF_ENOMEM);
+    if (cudaMemcpy(ctx->d_e2q.p, ctx->e2q.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->d_edges.p, ctx->edges.data(), sizeof(double) * (nb + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->d_nodes.p, ctx->nodes.data(), sizeof(double) * nb, cudaMemcpyHostToDevice) != cudaSuccess)
+        return cleanup(MP3PCF_ECUDA);
+    *out = ctx;
+    return MP3PCF_OK;
+}
+
+mp3pcf_status mp3pcf_destroy(mp3pcf_ctx* ctx)
+{
+    if (!ctx) return MP3PCF_OK;
+    cudaStreamSynchronize(ctx->st);
+    DevBuf* bufs[] = {&ctx->d_e2q, &ctx->d_edges, &ctx->d_nodes, &ctx->bb, &ctx->key,
+                      &ctx->count, &ctx->fill, &ctx->scan_sums, &ctx->scan_total, &ctx->perm,
+                      &ctx->pos, &ctx->pa, &ctx->pb, &ctx->pw, &ctx->zs, &ctx->cflag,
+                      &ctx->crank, &ctx->oflag, &ctx->orank, &ctx->centre_idx, &ctx->crow,
+                      &ctx->G, &ctx->W, &ctx->pairs, &ctx->partial, &ctx->singular,
+                      &ctx->m3partial};
+    for (DevBuf* b : bufs) b->release();
+    for (auto& pr : ctx->ev) {
+        cudaEventDestroy(pr.second.first);
+        cudaEventDestroy(pr.second.second);
+    }
+    for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+    delete ctx;
+    return MP3PCF_OK;
+}
+
+const char* mp3pcf_last_error(const mp3pcf_ctx* ctx)
+{
+    return ctx ? ctx->err.c_str() : "null context";
+}
+
+}  // extern "C"
+
+// exclusive scan of K ints from `in` to `out` (out has K+1 entries; out[K] = total)
+static mp3pcf_status scan_exclusive(mp3pcf_ctx* ctx, const int* in, int* out, int64_t K)
+{
+    const int64_t nblk = (K + kScanBlock - 1) / kScanBlock;
+    ctx->launches[ST_SORT] += nblk > 0 ? 3 : 1;
+    MP3_CK(ctx->scan_sums.ensure(sizeof(int) * (nblk + 1)));
+    if (nblk > 0) {
+        k_scan_blocks<<<(unsigned)nblk, 256, 0, ctx->st>>>(in, out, K, ctx->scan_sums.as<int>());
+        MP3_CK(cudaGetLastError());
+    }
+    k_scan_sums<<<1, 1024, 0, ctx->st>>>(ctx->scan_sums.as<int>(), (int)nblk, out + K);
+    MP3_CK(cudaGetLastError());
+    if (nblk > 0) {
+        k_scan_add<<<(unsigned)nblk, 256, 0, ctx->st>>>(out, K, ctx->scan_sums.as<int>());
+        MP3_CK(cudaGetLastError());
+    }
+    return MP3PCF_OK;
+}
+
+static unsigned grid1d(int64_t n, int n_sm)
+{
+    int64_t g = (n + 255) / 256;
+    const int64_t cap = (int64_t)n_sm * 16;
+    if (g > cap) g = cap;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+template <typename T>
+static mp3pcf_status accumulate_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq, const int32_t* yq,
+                                  const float* g1, const float* g2, const float* w,
+                                  const uint8_t* zb, const uint8_t* mask)
+{
+    const mp3pcf_config& c = ctx->cfg;
+    const int nz = c.n_z, nb = c.n_bins;
+    cudaStream_t st = ctx->st;
+    ctx->n = n;
+    ctx->n_centres = 0;
+    MP3_CK(cudaMemsetAsync(ctx->pairs.p, 0, 8, st));
+    if (n == 0) return MP3PCF_OK;
+
+    // ---- extent of the catalog (one host round trip)
+    cudaEvent_t t_sort = stage_begin(ctx);
+    ctx->launches[ST_SORT] += 2;
+    k_bbox_init<<<1, 1, 0, st>>>(ctx->bb.as<int>());
+    k_bbox<<<grid1d(n, ctx->n_sm), 256, 0, st>>>(n, xq, yq, zb, nz, ctx->bb.as<int>());
+    MP3_CK(cudaGetLastError());
+    int bb[5];
+    MP3_CK(cudaMemcpyAsync(bb, ctx->bb.p, sizeof(bb), cudaMemcpyDeviceToHost, st));
+    MP3_CK(cudaStreamSynchronize(st));
+    if (bb[4]) {
+        stage_end(ctx, ST_SORT, t_sort);
+        return fail(ctx, MP3PCF_EINVAL, "zbin value >= n_z");
+    }
+    const long long ex = (long long)bb[2] - bb[0], ey = (long long)bb[3] - bb[1];
+    if (ex >= (1LL << 24) || ey >= (1LL << 24)) {
+        stage_end(ctx, ST_SORT, t_sort);
+        return fail(ctx, MP3PCF_EINVAL, "patch extent must be below 2^24 position quanta");
+    }
+
+    // ---- cell grid: ~4 galaxies per cell and bin, and at most kMaxRows rows per annulus
+    const double R = sqrt((double)ctx->e2q[nb]);
+    const double area = (double)(ex + 1) * (double)(ey + 1);
+    double side = sqrt(area * 4.0 / std::max(1.0, (double)n / nz));
+    side = std::max(side, (2.0 * R + 16.0) / (kMaxRows - 4));
+    side = std::max(side, sqrt(area * nz / (double)(1 << 26)));
+    side = std::max(side, 1.0);
+    GridDesc g;
+    g.x0 = bb[0];
+    g.y0 = bb[1];
+    g.side = (int32_t)ceil(side);
+    g.ncx = (int32_t)(ex / g.side + 1);
+    g.ncy = (int32_t)(ey / g.side + 1);
+    g.ncells = g.ncx * g.ncy;
+    ctx->grid = g;
+    const int64_t K = (int64_t)nz * g.ncells;
+
+    // ---- counting sort by (zbin, cell)
+    MP3_CK(ctx->key.ensure(sizeof(int) * n));
+    MP3_CK(ctx->count.ensure(sizeof(int) * (K + 1)));
+    MP3_CK(ctx->fill.ensure(sizeof(int) * (K + 1)));
+    MP3_CK(ctx->perm.ensure(sizeof(int) * n));
+    MP3_CK(ctx->pos.ensure(sizeof(int2) * n));
+    MP3_CK(ctx->pa.ensure(sizeof(T) * n));
+    MP3_CK(ctx->pb.ensure(sizeof(T) * n));
+    MP3_CK(ctx->pw.ensure(sizeof(T) * n));
+    MP3_CK(ctx->zs.ensure(n));
+    MP3_CK(ctx->cflag.ensure(sizeof(int) * (n + 1)));
+    MP3_CK(ctx->crank.ensure(sizeof(int) * (n + 1)));
+    MP3_CK(ctx->oflag.ensure(sizeof(int) * (n + 1)));
+    MP3_CK(ctx->orank.ensure(sizeof(int) * (n + 1)));
+    MP3_CK(ctx->centre_idx.ensure(sizeof(int) * n));
+    MP3_CK(ctx->crow.ensure(sizeof(int) * n));
+    MP3_CK(cudaMemsetAsync(ctx->fill.p, 0, sizeof(int) * (K + 1), st));
+    ctx->launches[ST_SORT] += 6;
+    k_keys<<<grid1d(n, ctx->n_sm), 256, 0, st>>>(n, xq, yq, zb, g, ctx->key.as<int>(), ctx->fill.as<int>());
+    MP3_CK(cudaGetLastError());
+    if (mp3pcf_status s = scan_exclusive(ctx, ctx->fill.as<int>(), ctx->count.as<int>(), K)) return s;
+    MP3_CK(cudaMemsetAsync(ctx->fill.p, 0, sizeof(int) * (K + 1), st));
+    k_scatter<<<grid1d(n, ctx->n_sm), 256, 0, st>>>(n, ctx->key.as<int>(), ctx->count.as<int>(),
+                                                    ctx->fill.as<int>(), ctx->perm.as<int>());
+    k_cell_order<<<grid1d(K, ctx->n_sm), 256, 0, st>>>(K, ctx->count.as<int>(), ctx->perm.as<int>());
+    k_gather<T><<<grid1d(n, ctx->n_sm), 256, 0, st>>>(
+        n, ctx->perm.as<int>(), xq, yq, g1, g2, w, zb, mask, ctx->pos.as<int2>(), ctx->pa.as<T>(),
+        ctx->pb.as<T>(), ctx->pw.as<T>(), ctx->zs.as<uint8_t>(), ctx->cflag.as<int>());
+    MP3_CK(cudaGetLastError());
+
+    // ---- centre list (sorted order) and each centre's row in galaxy-index order
+    if (mp3pcf_status s = scan_exclusive(ctx, ctx->cflag.as<int>(), ctx->crank.as<int>(), n)) return s;
+    k_mask_flags<<<grid1d(n, ctx->n_sm), 256, 0, st>>>(n, mask, ctx->oflag.as<int>());
+    if (mp3pcf_status s = scan_exclusive(ctx, ctx->oflag.as<int>(), ctx->orank.as<int>(), n)) return s;
+    k_centres<<<grid1d(n, ctx->n_sm), 256, 0, st>>>(n, ctx->perm.as<int>(), ctx->cflag.as<int>(),
+                                                    ctx->crank.as<int>(), ctx->orank.as<int>(),
+                                                    ctx->centre_idx.as<int>(), ctx->crow.as<int>());
+    MP3_CK(cudaGetLastError());
+    int nc = (int)n;
+    if (mask) {
+        MP3_CK(cudaMemcpyAsync(&nc, ctx->crank.as<int>() + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MP3_CK(cudaStreamSynchronize(st));
+    }
+    ctx->n_centres = nc;
+    stage_end(ctx, ST_SORT, t_sort);
+    if (nc == 0) return MP3PCF_OK;
+
+    // ---- stage (a)
+    const int MG = 2 * c.n_max + 3, MW = 2 * c.n_max + 1;
+    MP3_CK(ctx->G.ensure(sizeof(cx<T>) * (size_t)nc * nz * nb * MG));
+    MP3_CK(ctx->W.ensure(sizeof(cx<T>) * (size_t)nc * nz * nb * MW));
+    MomentArgs<T> a;
+    a.n_centres = nc;
+    a.centre_idx = ctx->centre_idx.as<int>();
+    a.pos = ctx->pos.as<int2>();
+    a.pa = ctx->pa.as<T>();
+    a.pb = ctx->pb.as<T>();
+    a.pw = ctx->pw.as<T>();
+    a.cell_start = ctx->count.as<int>();
+    a.g = g;
+    a.nz = nz;
+    a.nb = nb;
+    a.n_max = c.n_max;
+    a.e2q = ctx->d_e2q.as<long long>();
+    a.G = ctx->G.as<cx<T>>();
+    a.W = ctx->W.as<cx<T>>();
+    a.pairs = ctx->pairs.as<unsigned long long>();
+    cudaError_t e;
+    {
+        StageScope sc(ctx, ST_MOMENTS);
+        ctx->launches[ST_MOMENTS] += 1;
+        if constexpr (sizeof(T) == 8)
+            e = launch_moments_f64(a, ctx->n_sm, st);
+        else
+            e = launch_moments_f32(a, ctx->n_sm, st);
+    }
+    MP3_CK(e);
+    return MP3PCF_OK;
+}
+
+extern "C" {
+
+mp3pcf_status mp3pcf_accumulate_moments(mp3pcf_ctx* ctx, int64_t n, const int32_t* d_xq,
+                                        const int32_t* d_yq, const float* d_g1, const float* d_g2,
+                                        const float* d_w, const uint8_t* d_zbin,
+                                        const uint8_t* d_centre_mask)
+{
+    if (!ctx) return MP3PCF_EINVAL;
+    ctx->err.clear();
+    if (n < 0 || n > INT_MAX / 2) return fail(ctx, MP3PCF_EINVAL, "n out of range");
+    if (n > 0 && (!d_xq || !d_yq || !d_g1 || !d_g2 || !d_w))
+        return fail(ctx, MP3PCF_EINVAL, "null catalog pointer");
+    if (ctx->cfg.n_z > 1 && n > 0 && !d_zbin)
+        return fail(ctx, MP3PCF_EINVAL, "n_z > 1 needs zbin");
+    if (ctx->fp64) return accumulate_t<double>(ctx, n, d_xq, d_yq, d_g1, d_g2, d_w, d_zbin, d_centre_mask);
+    return accumulate_t<float>(ctx, n, d_xq, d_yq, d_g1, d_g2, d_w, d_zbin, d_centre_mask);
+}
+
+mp3pcf_status mp3pcf_counts(mp3pcf_ctx* ctx, int64_t* h_n_centres, int64_t* h_n_pairs)
+{
+    if (!ctx) return MP3PCF_EINVAL;
+    if (h_n_centres) *h_n_centres = ctx->n_centres;
+    if (h_n_pairs) {
+        unsigned long long p = 0;
+        MP3_CK(cudaMemcpyAsync(&p, ctx->pairs.p, 8, cudaMemcpyDeviceToHost, ctx->st));
+        MP3_CK(cudaStreamSynchronize(ctx->st));
+        *h_n_pairs = (int64_t)p;
+    }
+    return MP3PCF_OK;
+}
+
+mp3pcf_status mp3pcf_copy_moments(mp3pcf_ctx* ctx, void* d_G, void* d_W)
+{
+    if (!ctx) return MP3PCF_EINVAL;
+    ctx->err.clear();
+    const int64_t nc = ctx->n_centres;
+    if (nc == 0) return MP3PCF_OK;
+    const mp3pcf_config& c = ctx->cfg;
+    const int rg = c.n_z * c.n_bins * (2 * c.n_max + 3), rw = c.n_z * c.n_bins * (2 * c.n_max + 1);
+    const unsigned gr = grid1d(nc * rg, ctx->n_sm);
+    if (ctx->fp64) {
+        if (d_G) k_copy_rows<double><<<gr, 256, 0, ctx->st>>>(nc, rg, ctx->crow.as<int>(), ctx->G.as<cx<double>>(), (cx<double>*)d_G);
+        if (d_W) k_copy_rows<double><<<gr, 256, 0, ctx->st>>>(nc, rw, ctx->crow.as<int>(), ctx->W.as<cx<double>>(), (cx<double>*)d_W);
+    } else {
+        if (d_G) k_copy_rows<float><<<gr, 256, 0, ctx->st>>>(nc, rg, ctx->crow.as<int>(), ctx->G.as<cx<float>>(), (cx<float>*)d_G);
+        if (d_W) k_copy_rows<float><<<gr, 256, 0, ctx->st>>>(nc, rw, ctx->crow.as<int>(), ctx->W.as<cx<float>>(), (cx<float>*)d_W);
+    }
+    MP3_CK(cudaGetLastError());
+    return MP3PCF_OK;
+}
+
+mp3pcf_status mp3pcf_contract_multipoles(mp3pcf_ctx* ctx, double* d_upsilon, double* d_norm)
+{
+    if (!ctx || !d_upsilon || !d_norm) return fail(ctx, MP3PCF_EINVAL, "null argument");
+    ctx->err.clear();
+    const mp3pcf_config& c = ctx->cfg;
+    if (c.precision == MP3PCF_FP32_BF16X3 || c.precision == MP3PCF_FP32_TF32X3)
+        return fail(ctx, MP3PCF_EUNSUPPORTED, "tensor-core contraction not built");
+    const int64_t nc = ctx->n_centres;
+    if (nc == 0) return MP3PCF_OK;
+    const int nz = c.n_z, nb = c.n_bins;
+    const int z3 = nz * nz * nz;
+    const int groups = z3 * groups_per_zt(c.n_max);
+    int splits = (int)std::min<int64_t>(64, std::max<int64_t>(1, (int64_t)ctx->n_sm * 8 / groups));
+    splits = (int)std::min<int64_t>(splits, std::max<int64_t>(1, nc / 256));
+    MP3_CK(ctx->partial.ensure(sizeof(double) * 2 * (size_t)splits * groups * nb * nb));
+    StageScope sc(ctx, ST_CONTRACT);
+    ctx->launches[ST_CONTRACT] += 2;
+    cudaError_t e;
+    if (ctx->fp64) {
+        ContractArgs<double> a{ctx->G.as<cx<double>>(), ctx->W.as<cx<double>>(), ctx->pa.as<double>(),
+                               ctx->pb.as<double>(), ctx->pw.as<double>(), ctx->zs.as<uint8_t>(),
+                               ctx->centre_idx.as<int>(), (int32_t)nc, nz, nb, c.n_max, splits,
+                               ctx->partial.as<double>()};
+        e = launch_contract_f64(a, ctx->st);
+    } else {
+        ContractArgs<float> a{ctx->G.as<cx<float>>(), ctx->W.as<cx<float>>(), ctx->pa.as<float>(),
+                              ctx->pb.as<float>(), ctx->pw.as<float>(), ctx->zs.as<uint8_t>(),
+                              ctx->centre_idx.as<int>(), (int32_t)nc, nz, nb, c.n_max, splits,
+                              ctx->partial.as<double>()};
+        e = launch_contract_f32(a, ctx->st);
+    }
+    MP3_CK(e);
+    MP3_CK(launch_contract_reduce(ctx->partial.as<double>(), splits, nz, nb, c.n_max, d_upsilon, d_norm, ctx->st));
+    return MP3PCF_OK;
+}
+
+static PostArgs post_args(mp3pcf_ctx* ctx)
+{
+    const mp3pcf_config& c = ctx->cfg;
+    PostArgs p;
+    p.nz = c.n_z;
+    p.nb = c.n_bins;
+    p.n_max = c.n_max;
+    p.n_phi = c.n_phi;
+    p.norm_truncate = c.norm_truncate;
+    p.edges = ctx->d_edges.as<double>();
+    p.nodes = ctx->d_nodes.as<double>();
+    return p;
+}
+
+mp3pcf_status mp3pcf_edge_correct(mp3pcf_ctx* ctx, const double* d_upsilon, const double* d_norm,
+                                  double* d_gamma_n, int64_t* h_n_singular)
+{
+    if (!ctx || !d_upsilon || !d_norm || !d_gamma_n) return fail(ctx, MP3PCF_EINVAL, "null argument");
+    ctx->err.clear();
+    MP3_CK(cudaMemsetAsync(ctx->singular.p, 0, 8, ctx->st));
+    {
+        StageScope sc(ctx, ST_EDGE);
+        ctx->launches[ST_EDGE] += 1;
+        MP3_CK(launch_edge_correct(post_args(ctx), d_upsilon, d_norm, d_gamma_n,
+                                   ctx->singular.as<unsigned long long>(), ctx->st));
+    }
+    if (h_n_singular) {
+        unsigned long long ns = 0;
+        MP3_CK(cudaMemcpyAsync(&ns, ctx->singular.p, 8, cudaMemcpyDeviceToHost, ctx->st));
+        MP3_CK(cudaStreamSynchronize(ctx->st));
+        *h_n_singular = (int64_t)ns;
+        if (ns) return fail(ctx, MP3PCF_ESINGULAR, "singular mode-coupling systems");
+    }
+    return MP3PCF_OK;
+}
+
+mp3pcf_status mp3pcf_to_gamma(mp3pcf_ctx* ctx, const double* d_gamma_n, int32_t projection,
+                              double* d_gamma_phi)
+{
+    if (!ctx || !d_gamma_n || !d_gamma_phi || (projection != 0 && projection != 1))
+        return fail(ctx, MP3PCF_EINVAL, "bad argument");
+    ctx->err.clear();
+    StageScope sc(ctx, ST_GAMMA);
+    ctx->launches[ST_GAMMA] += 1;
+    MP3_CK(launch_to_gamma(post_args(ctx), d_gamma_n, projection, d_gamma_phi, ctx->st));
+    return MP3PCF_OK;
+}
+
+mp3pcf_status mp3pcf_to_map3(mp3pcf_ctx* ctx, const double* d_gamma_cen, int64_t n_ap,
+                             const double* d_theta_ap, double* d_corr, double* d_m8)
+{
+    if (!ctx || !d_gamma_cen || n_ap < 0 || n_ap > 65535 || (n_ap > 0 && !d_theta_ap))
+        return fail(ctx, MP3PCF_EINVAL, "bad argument");
+    ctx->err.clear();
+    if (n_ap == 0) return MP3PCF_OK;
+    const mp3pcf_config& c = ctx->cfg;
+    const int z3 = c.n_z * c.n_z * c.n_z;
+    const int chunks = 64;
+    MP3_CK(ctx->m3partial.ensure(sizeof(double) * 8 * (size_t)z3 * n_ap * chunks));
+    StageScope sc(ctx, ST_MAP3);
+    ctx->launches[ST_MAP3] += 2;
+    MP3_CK(launch_to_map3(post_args(ctx), d_gamma_cen, (int)n_ap, d_theta_ap,
+                          ctx->m3partial.as<double>(), chunks, d_corr, d_m8, ctx->st));
+    return MP3PCF_OK;
+}
+
+mp3pcf_status mp3pcf_set_timing(mp3pcf_ctx* ctx, int32_t on)
+{
+    if (!ctx) return MP3PCF_EINVAL;
+    ctx->timing = on != 0;
+    return MP3PCF_OK;
+}
+
+mp3pcf_status mp3pcf_stage_times(mp3pcf_ctx* ctx, double* h_ms, int64_t* h_launches, int32_t reset)
+{
+    if (!ctx) return MP3PCF_EINVAL;
+    MP3_CK(cudaStreamSynchronize(ctx->st));
+    double ms[6] = {0, 0, 0, 0, 0, 0};
+    for (auto& pr : ctx->ev) {
+        float t = 0.f;
+        MP3_CK(cudaEventElapsedTime(&t, pr.second.first, pr.second.second));
+        ms[pr.first] += t;
+    }
+    for (int i = 0; i < 6; ++i) {
+        if (h_ms) h_ms[i] = ms[i];
+        if (h_launches) h_launches[i] = ctx->launches[i];
+    }
+    if (reset) {
+        for (auto& pr : ctx->ev) {
+            ctx->pool.push_back(pr.second.first);
+            ctx->pool.push_back(pr.second.second);
+        }
+        ctx->ev.clear();
+        for (int i = 0; i < 6; ++i) ctx->launches[i] = 0;
+    }
+    return MP3PCF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,137 @@
+// Shared device/host definitions of the mp3pcf CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mp3pcf.h"
+
+namespace mp3 {
+
+constexpr int kMaxBins = 64;   // radial bins supported by the device kernels
+constexpr int kMaxNmax = 50;   // largest multipole order
+constexpr int kMaxNz = 8;      // tomographic bins
+constexpr int kMaxRows = 512;  // cell rows an annulus may span (host picks the cell side)
+
+// ------------------------------------------------------------------ complex helpers
+
+template <typename T>
+struct cx {
+    T x, y;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b)
+{
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> cconj(cx<T> a)
+{
+    return {a.x, -a.y};
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b)
+{
+    return {a.x + b.x, a.y + b.y};
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b)
+{
+    return {a.x - b.x, a.y - b.y};
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> cscale(cx<T> a, T s)
+{
+    return {a.x * s, a.y * s};
+}
+
+__host__ __device__ __forceinline__ cx<double> cdiv(cx<double> a, cx<double> b)
+{
+    // (a b*) / |b|^2 with a scaling step against overflow
+    const double s = fabs(b.x) > fabs(b.y) ? fabs(b.x) : fabs(b.y);
+    const double bx = b.x / s, by = b.y / s;
+    const double d = bx * bx + by * by;
+    return {(a.x * bx + a.y * by) / (d * s), (a.y * bx - a.x * by) / (d * s)};
+}
+
+// ------------------------------------------------------------------ geometry of the cell grid
+
+struct GridDesc {
+    int64_t x0, y0;     // fixed-point origin of cell (0, 0)
+    int32_t side;       // cell side in fixed-point units
+    int32_t ncx, ncy;   // cells per row / rows
+    int32_t ncells;     // ncx * ncy (per tomographic bin)
+};
+
+// ------------------------------------------------------------------ stage (a) arguments
+
+template <typename T>
+struct MomentArgs {
+    int32_t n_centres;
+    const int32_t* centre_idx;  // sorted position of each centre
+    const int2* pos;            // sorted fixed-point positions
+    const T* pa;                // sorted w * gamma_1
+    const T* pb;                // sorted w * gamma_2
+    const T* pw;                // sorted w
+    const int32_t* cell_start;  // [n_z * ncells + 1], key = zbin * ncells + cy * ncx + cx
+    GridDesc g;
+    int32_t nz, nb, n_max;
+    const long long* e2q;       // [nb + 1] exact squared edges in fixed-point units^2
+    cx<T>* G;                   // [n_centres][nz][nb][2 n_max + 3]
+    cx<T>* W;                   // [n_centres][nz][nb][2 n_max + 1]
+    unsigned long long* pairs;  // pair counter
+};
+
+// launchers implemented in moments_f32.cu / moments_f64.cu
+cudaError_t launch_moments_f32(const MomentArgs<float>& a, int n_sm, cudaStream_t st);
+cudaError_t launch_moments_f64(const MomentArgs<double>& a, int n_sm, cudaStream_t st);
+
+// ------------------------------------------------------------------ stage (b)
+
+template <typename T>
+struct ContractArgs {
+    const cx<T>* G;
+    const cx<T>* W;
+    const T* pa;               // sorted w gamma_1
+    const T* pb;               // sorted w gamma_2
+    const T* pw;               // sorted w
+    const uint8_t* zs;         // sorted zbin
+    const int32_t* centre_idx; // sorted position of each centre (row order of G, W)
+    int32_t n_centres;
+    int32_t nz, nb, n_max;
+    int32_t splits;
+    double* partial;  // [splits][groups][nb*nb][2]
+};
+
+cudaError_t launch_contract_f32(const ContractArgs<float>& a, cudaStream_t st);
+cudaError_t launch_contract_f64(const ContractArgs<double>& a, cudaStream_t st);
+cudaError_t launch_contract_reduce(const double* partial, int splits, int nz, int nb, int n_max,
+                                   double* ups, double* norm, cudaStream_t st);
+
+// ------------------------------------------------------------------ post-processing (FP64)
+
+struct PostArgs {
+    int32_t nz, nb, n_max, n_phi, norm_truncate;
+    const double* edges;  // device, nb + 1 (arcmin)
+    const double* nodes;  // device, nb radial nodes
+};
+
+cudaError_t launch_edge_correct(const PostArgs& p, const double* ups, const double* norm,
+                                double* gam, unsigned long long* n_singular, cudaStream_t st);
+cudaError_t launch_to_gamma(const PostArgs& p, const double* gam, int projection, double* out,
+                            cudaStream_t st);
+cudaError_t launch_to_map3(const PostArgs& p, const double* gcen, int n_ap, const double* theta,
+                           double* partial, int chunks, double* corr, double* m8,
+                           cudaStream_t st);
+
+__host__ __device__ inline int groups_per_zt(int n_max) { return 4 * (n_max + 1) + 2 * n_max + 1; }
+
+}  // namespace mp3

@@ -1,0 +1,380 @@
+// FP64 stages after the contraction: the edge-correction solve (paper Sec. 3.4), the multipole
+// sum to Gamma^x(phi) and its conversion to the centroid projection (Sec. 2.2, Sec. 4), and the
+// aperture-measure integrals (Sec. 5.2, App. C).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace mp3 {
+
+// ------------------------------------------------------------------ c1: edge correction
+
+// Block per (Z-triplet, b1, b2). The (2 n_max + 1)^2 complex matrix N_{l-n} and the four
+// right-hand sides Upsilon_{mu,l} live in shared memory; Gaussian elimination with partial
+// pivoting (largest |pivot|, lowest row on ties), then back substitution by four warps.
+__global__ void __launch_bounds__(256) edge_correct_kernel(const PostArgs p, const double* __restrict__ ups,
+                                                           const double* __restrict__ norm,
+                                                           double* __restrict__ gam,
+                                                           unsigned long long* nsing)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nmax = p.n_max, D = 2 * nmax + 1, nb = p.nb, nz = p.nz;
+    const int NN = nmax + 1, NW = 2 * nmax + 1;
+    cx<double>* A = reinterpret_cast<cx<double>*>(smem_raw);
+    cx<double>* B = A + (size_t)D * D;
+    __shared__ double red_v[256];
+    __shared__ int red_i[256];
+    __shared__ int s_bad;
+    const int sys = blockIdx.x;
+    const int b2 = sys % nb, b1 = (sys / nb) % nb, zt = sys / (nb * nb);
+    const int z1 = zt / (nz * nz), z2 = (zt / nz) % nz, z3 = zt % nz;
+    const int zsw = (z1 * nz + z3) * nz + z2;
+    const int tid = threadIdx.x;
+    const cx<double>* U = reinterpret_cast<const cx<double>*>(ups);
+    const cx<double>* Nn = reinterpret_cast<const cx<double>*>(norm);
+
+    for (int idx = tid; idx < D * D; idx += blockDim.x) {
+        const int l = idx / D - nmax, nn = idx % D - nmax, m = l - nn;
+        cx<double> v{0.0, 0.0};
+        if (!(p.norm_truncate && (m > nmax || m < -nmax))) {
+            if (m >= 0)
+                v = Nn[(((size_t)zt * NW + m) * nb + b1) * nb + b2];
+            else
+                v = Nn[(((size_t)zsw * NW + (-m)) * nb + b2) * nb + b1];
+        }
+        A[idx] = v;
+    }
+    for (int idx = tid; idx < D * 4; idx += blockDim.x) {
+        const int l = idx / 4 - nmax, mu = idx % 4;
+        cx<double> v;
+        if (l >= 0) {
+            v = U[((((size_t)zt * 4 + mu) * NN + l) * nb + b1) * nb + b2];
+        } else {
+            const int mus = mu == 2 ? 3 : (mu == 3 ? 2 : mu);
+            v = U[((((size_t)zsw * 4 + mus) * NN + (-l)) * nb + b2) * nb + b1];
+        }
+        B[idx] = v;
+    }
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    if (tid == 0) {
+        const cx<double> n0 = A[(size_t)nmax * D + nmax];
+        if (n0.x == 0.0 && n0.y == 0.0) s_bad = 1;
+    }
+    __syncthreads();
+
+    for (int k = 0; k < D && !s_bad; ++k) {
+        double best = -1.0;
+        int bi = D;
+        for (int r = k + tid; r < D; r += blockDim.x) {
+            const cx<double> v = A[(size_t)r * D + k];
+            const double m2 = v.x * v.x + v.y * v.y;
+            if (m2 > best) {
+                best = m2;
+                bi = r;
+            }
+        }
+        red_v[tid] = best;
+        red_i[tid] = bi;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (tid < s) {
+                const double ov = red_v[tid + s];
+                const int oi = red_i[tid + s];
+                if (ov > red_v[tid] || (ov == red_v[tid] && oi < red_i[tid])) {
+                    red_v[tid] = ov;
+                    red_i[tid] = oi;
+                }
+            }
+            __syncthreads();
+        }
+        const int piv = red_i[0];
+        const bool zero = !(red_v[0] > 0.0);
+        __syncthreads();
+        if (zero) {
+            if (tid == 0) s_bad = 1;
+            __syncthreads();
+            break;
+        }
+        if (piv != k) {
+            for (int j = k + tid; j < D; j += blockDim.x) {
+                const cx<double> t = A[(size_t)k * D + j];
+                A[(size_t)k * D + j] = A[(size_t)piv * D + j];
+                A[(size_t)piv * D + j] = t;
+            }
+            for (int j = tid; j < 4; j += blockDim.x) {
+                const cx<double> t = B[k * 4 + j];
+                B[k * 4 + j] = B[piv * 4 + j];
+                B[piv * 4 + j] = t;
+            }
+        }
+        __syncthreads();
+        const cx<double> akk = A[(size_t)k * D + k];
+        const int rows = D - k - 1, cols = D - k - 1 + 4;
+        for (int idx = tid; idx < rows * cols; idx += blockDim.x) {
+            const int r = k + 1 + idx / cols, jj = idx % cols;
+            const cx<double> f = cdiv(A[(size_t)r * D + k], akk);
+            if (jj < D - k - 1) {
+                const int j = k + 1 + jj;
+                A[(size_t)r * D + j] = csub(A[(size_t)r * D + j], cmul(f, A[(size_t)k * D + j]));
+            } else {
+                const int mu = jj - (D - k - 1);
+                B[r * 4 + mu] = csub(B[r * 4 + mu], cmul(f, B[k * 4 + mu]));
+            }
+        }
+        __syncthreads();
+    }
+    const bool bad = s_bad != 0;
+    const int warp = tid >> 5, lane = tid & 31;
+    if (!bad && warp < 4) {
+        const int mu = warp;
+        for (int k = D - 1; k >= 0; --k) {
+            double sr = 0.0, si = 0.0;
+            for (int q = k + 1 + lane; q < D; q += 32) {
+                const cx<double> t = cmul(A[(size_t)k * D + q], B[q * 4 + mu]);
+                sr += t.x;
+                si += t.y;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                si += __shfl_xor_sync(0xffffffffu, si, o);
+            }
+            if (lane == 0) {
+                const cx<double> rhs{B[k * 4 + mu].x - sr, B[k * 4 + mu].y - si};
+                B[k * 4 + mu] = cdiv(rhs, A[(size_t)k * D + k]);
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    cx<double>* out = reinterpret_cast<cx<double>*>(gam);
+    for (int idx = tid; idx < D * 4; idx += blockDim.x) {
+        const int nn = idx / 4, mu = idx % 4;
+        out[((((size_t)zt * 4 + mu) * D + nn) * nb + b1) * nb + b2] =
+            bad ? cx<double>{nan(""), nan("")} : B[idx];
+    }
+    if (bad && tid == 0) atomicAdd(nsing, 1ULL);
+}
+
+cudaError_t launch_edge_correct(const PostArgs& p, const double* ups, const double* norm,
+                                double* gam, unsigned long long* nsing, cudaStream_t st)
+{
+    const int D = 2 * p.n_max + 1;
+    const size_t smem = sizeof(cx<double>) * ((size_t)D * D + (size_t)D * 4);
+    cudaError_t e = cudaFuncSetAttribute(edge_correct_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int systems = p.nz * p.nz * p.nz * p.nb * p.nb;
+    edge_correct_kernel<<<systems, 256, smem, st>>>(p, ups, norm, gam, nsing);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ c2: to_gamma
+
+// rotation factor taking Gamma^x_mu to Gamma^cen_mu at (t1, t2, phi), e = e^{i phi}
+__device__ __forceinline__ cx<double> centroid_factor(int mu, double t1, double t2, cx<double> e)
+{
+    const cx<double> ec = cconj(e);
+    const cx<double> r1 = cdiv(cx<double>{t1 + t2 * ec.x, t2 * ec.y}, cx<double>{t1 + t2 * e.x, t2 * e.y});
+    const cx<double> r2 = cdiv(cx<double>{t2 * ec.x - 2.0 * t1, t2 * ec.y},
+                               cx<double>{t2 * e.x - 2.0 * t1, t2 * e.y});
+    const cx<double> r3 = cdiv(cx<double>{t1 - 2.0 * t2 * ec.x, -2.0 * t2 * ec.y},
+                               cx<double>{t1 - 2.0 * t2 * e.x, -2.0 * t2 * e.y});
+    const cx<double> e2 = cmul(e, e), e3 = cmul(e2, e);
+    switch (mu) {
+        case 0: return cmul(cmul(cmul(r1, r2), r3), e3);
+        case 1: return cmul(cdiv(cmul(r2, r3), r1), e);
+        case 2: return cmul(cdiv(cmul(r1, r3), r2), e3);
+        default: return cmul(cdiv(cmul(r1, r2), r3), ec);
+    }
+}
+
+__global__ void to_gamma_kernel(const PostArgs p, const double* __restrict__ gam, int proj,
+                                double* __restrict__ out)
+{
+    const int nb = p.nb, nmax = p.n_max, D = 2 * nmax + 1, np = p.n_phi;
+    const int z3 = p.nz * p.nz * p.nz;
+    const int64_t total = (int64_t)z3 * 4 * nb * nb * np;
+    const cx<double>* G = reinterpret_cast<const cx<double>*>(gam);
+    cx<double>* O = reinterpret_cast<cx<double>*>(out);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(t % np);
+        const int64_t rest = t / np;
+        const int b2 = (int)(rest % nb), b1 = (int)((rest / nb) % nb);
+        const int64_t zm = rest / ((int64_t)nb * nb);  // zt * 4 + mu
+        double s, c;
+        sincospi((2.0 * k + 1.0) / np, &s, &c);
+        const cx<double> e1{c, s};
+        const size_t stride = (size_t)nb * nb;
+        const cx<double>* g0 = G + (size_t)zm * D * stride + (size_t)b1 * nb + b2;
+        cx<double> acc = g0[(size_t)nmax * stride];
+        cx<double> ep{1.0, 0.0};
+        for (int n = 1; n <= nmax; ++n) {
+            ep = cmul(ep, e1);
+            acc = cadd(acc, cmul(g0[(size_t)(nmax + n) * stride], ep));
+            acc = cadd(acc, cmul(g0[(size_t)(nmax - n) * stride], cconj(ep)));
+        }
+        if (proj) acc = cmul(acc, centroid_factor((int)(zm % 4), p.nodes[b1], p.nodes[b2], e1));
+        O[t] = acc;
+    }
+}
+
+cudaError_t launch_to_gamma(const PostArgs& p, const double* gam, int projection, double* out,
+                            cudaStream_t st)
+{
+    const int64_t total = (int64_t)p.nz * p.nz * p.nz * 4 * p.nb * p.nb * p.n_phi;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    if (blocks < 1) blocks = 1;
+    to_gamma_kernel<<<(unsigned)blocks, 256, 0, st>>>(p, gam, projection, out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ c3: to_map3
+
+// The four filters. F_0 as printed in App. C. For mu = 1..3 (conjugate at vertex mu) the
+// printed F_1 expression is evaluated with its three vertex labels rotated by
+// s = (mu + 1) mod 3: with the q-vectors of Eq. QvecDef the printed expression is the kernel of
+// the correlator conjugated at vertex 2 (derived from Eqs. MapGamma, CrittendenQ and the
+// centroid projection), so rotating by s moves its special vertex onto vertex mu.
+__device__ cx<double> aperture_filter(int mu, double t1, double t2, cx<double> e, const double th[3])
+{
+    const cx<double> v1{t1, 0.0}, v2{t2 * e.x, t2 * e.y};
+    cx<double> q[3];
+    q[0] = cx<double>{-(v1.x + v2.x) / 3.0, -(v1.y + v2.y) / 3.0};
+    q[1] = cx<double>{(2.0 * v1.x - v2.x) / 3.0, (2.0 * v1.y - v2.y) / 3.0};
+    q[2] = cx<double>{(2.0 * v2.x - v1.x) / 3.0, (2.0 * v2.y - v1.y) / 3.0};
+    double s2[3], qq[3];
+    for (int i = 0; i < 3; ++i) {
+        s2[i] = th[i] * th[i];
+        qq[i] = q[i].x * q[i].x + q[i].y * q[i].y;
+    }
+    const double T4 = (s2[0] * s2[1] + s2[0] * s2[2] + s2[1] * s2[2]) / 3.0;
+    const double T2 = sqrt(T4), T6 = T2 * T4;
+    const double Mfac = (s2[0] * s2[1] * s2[2] / T6) * t1 * t2 / (2.0 * M_PI * T4);
+    double Z = 0.0;
+    cx<double> f[3], gg[3];
+    for (int i = 0; i < 3; ++i) {
+        const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+        Z += (-s2[i] + 2.0 * s2[i1] + 2.0 * s2[i2]) * qq[i];
+        const cx<double> r = cscale(cmul(cconj(q[i]), csub(q[i1], q[i2])), 1.0 / qq[i]);
+        f[i] = cx<double>{(s2[i1] + s2[i2]) / (2.0 * T2) + r.x * (s2[i1] - s2[i2]) / (6.0 * T2),
+                          r.y * (s2[i1] - s2[i2]) / (6.0 * T2)};
+        gg[i] = cx<double>{s2[i1] * s2[i2] / T4 + r.x * s2[i] * (s2[i2] - s2[i1]) / (3.0 * T4),
+                           r.y * s2[i] * (s2[i2] - s2[i1]) / (3.0 * T4)};
+    }
+    Z /= 6.0 * T4;
+    const double aq = qq[0] * qq[1] * qq[2];
+    const double ez = exp(-Z);
+    if (mu == 0) {
+        cx<double> pr{1.0, 0.0};
+        for (int i = 0; i < 3; ++i) {
+            const cx<double> fc = cconj(f[i]);
+            pr = cmul(pr, cmul(fc, fc));
+        }
+        return cscale(pr, Mfac / 24.0 * aq / T6 * ez);
+    }
+    const int s = (mu + 1) % 3;
+    const int u1 = s, u2 = (s + 1) % 3, u3 = (s + 2) % 3;
+    const cx<double> Q1 = q[u1], Q2c = cconj(q[u2]), Q3 = q[u3];
+    const cx<double> F1c = cconj(f[u1]), F2 = f[u2], F3c = cconj(f[u3]), G2c = cconj(gg[u2]);
+    const cx<double> q31 = cmul(Q3, Q1), q2c2 = cmul(Q2c, Q2c);
+    const cx<double> f31 = cmul(F3c, F1c);
+    // term 1: |q1|^2|q2|^2|q3|^2 / (24 Theta^6) f3*^2 f1*^2 f2^2
+    cx<double> t = cscale(cmul(cmul(f31, f31), cmul(F2, F2)), aq / (24.0 * T6));
+    // term 2: -(1/9) q3 q1 q2*^2 / Theta^4 f3* f1* f2 g2*
+    t = csub(t, cscale(cmul(cmul(q31, q2c2), cmul(cmul(f31, F2), G2c)), 1.0 / (9.0 * T4)));
+    // term 3: (1/27) [q3^2 q1^2 q2*^4 / (|q1|^2|q2|^2|q3|^2 Theta^2) g2*^2
+    //                 + 2 theta3^2 theta1^2 / Theta^4  q3 q1 q2*^2 / (|q2|^2 Theta^2) f3* f1*]
+    const cx<double> a1 = cscale(cmul(cmul(cmul(q31, q31), cmul(q2c2, q2c2)), cmul(G2c, G2c)), 1.0 / (aq * T2));
+    const cx<double> a2 = cscale(cmul(cmul(q31, q2c2), f31), 2.0 * s2[u3] * s2[u1] / (T4 * qq[u2] * T2));
+    t = cadd(t, cscale(cadd(a1, a2), 1.0 / 27.0));
+    return cscale(t, Mfac * ez);
+}
+
+constexpr int kM3Threads = 256;
+
+__global__ void __launch_bounds__(kM3Threads) map3_partial_kernel(const PostArgs p, const double* __restrict__ gcen,
+                                                                  int n_ap, const double* __restrict__ theta,
+                                                                  double* __restrict__ partial, int chunks)
+{
+    const int nb = p.nb, np = p.n_phi;
+    const int job = blockIdx.x;  // zt * n_ap + ap
+    const int zt = job / n_ap, ap = job % n_ap;
+    const int64_t npts = (int64_t)4 * nb * nb * np;
+    const int64_t per = (npts + chunks - 1) / chunks;
+    const int64_t p0 = blockIdx.y * per, p1 = min(npts, p0 + per);
+    const double th[3] = {theta[3 * ap], theta[3 * ap + 1], theta[3 * ap + 2]};
+    const double dphi = 2.0 * M_PI / np;
+    const cx<double>* gc = reinterpret_cast<const cx<double>*>(gcen) + (size_t)zt * npts;
+    double acc[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int64_t t = p0 + threadIdx.x; t < p1; t += blockDim.x) {
+        const int k = (int)(t % np);
+        const int64_t rest = t / np;
+        const int b2 = (int)(rest % nb), b1 = (int)((rest / nb) % nb), mu = (int)(rest / ((int64_t)nb * nb));
+        double s, c;
+        sincospi((2.0 * k + 1.0) / np, &s, &c);
+        const double t1 = p.nodes[b1], t2 = p.nodes[b2];
+        const double w = (p.edges[b1 + 1] - p.edges[b1]) * (p.edges[b2 + 1] - p.edges[b2]) * dphi;
+        const cx<double> v = cmul(gc[t], aperture_filter(mu, t1, t2, cx<double>{c, s}, th));
+        for (int q = 0; q < 4; ++q)
+            if (q == mu) {
+                acc[q][0] += v.x * w;
+                acc[q][1] += v.y * w;
+            }
+    }
+    __shared__ double red[kM3Threads / 32][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = 0; q < 4; ++q)
+        for (int r = 0; r < 2; ++r) {
+            double v = acc[q][r];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][2 * q + r] = v;
+        }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        double v = 0.0;
+        for (int wi = 0; wi < kM3Threads / 32; ++wi) v += red[wi][threadIdx.x];
+        partial[((size_t)job * chunks + blockIdx.y) * 8 + threadIdx.x] = v;
+    }
+}
+
+__global__ void map3_final_kernel(int jobs, int chunks, const double* __restrict__ partial,
+                                  double* __restrict__ corr, double* __restrict__ m8)
+{
+    const int job = blockIdx.x * blockDim.x + threadIdx.x;
+    if (job >= jobs) return;
+    double c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int ch = 0; ch < chunks; ++ch)
+        for (int q = 0; q < 8; ++q) c[q] += partial[((size_t)job * chunks + ch) * 8 + q];
+    if (corr)
+        for (int q = 0; q < 8; ++q) corr[(size_t)job * 8 + q] = c[q];
+    if (m8) {
+        // c0 = <M^3>, c1 = <M* M^2>, c2 = <M M* M>, c3 = <M^2 M*>; Eqs. MapTrafo8_1-8
+        const double r0 = c[0], i0 = c[1], r1 = c[2], i1 = c[3], r2 = c[4], i2 = c[5], r3 = c[6], i3 = c[7];
+        double* o = m8 + (size_t)job * 8;
+        o[0] = (r3 + r2 + r1 + r0) / 4.0;
+        o[1] = (i3 + i2 - i1 + i0) / 4.0;
+        o[2] = (i3 - i2 + i1 + i0) / 4.0;
+        o[3] = (-i3 + i2 + i1 + i0) / 4.0;
+        o[4] = (r3 + r2 - r1 - r0) / 4.0;
+        o[5] = (r3 - r2 + r1 - r0) / 4.0;
+        o[6] = (-r3 + r2 + r1 - r0) / 4.0;
+        o[7] = (i3 + i2 + i1 - i0) / 4.0;
+    }
+}
+
+cudaError_t launch_to_map3(const PostArgs& p, const double* gcen, int n_ap, const double* theta,
+                           double* partial, int chunks, double* corr, double* m8, cudaStream_t st)
+{
+    const int jobs = p.nz * p.nz * p.nz * n_ap;
+    dim3 grid(jobs, chunks);
+    map3_partial_kernel<<<grid, kM3Threads, 0, st>>>(p, gcen, n_ap, theta, partial, chunks);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    map3_final_kernel<<<(jobs + 127) / 128, 128, 0, st>>>(jobs, chunks, partial, corr, m8);
+    return cudaGetLastError();
+}
+
+}  // namespace mp3
