@@ -97,9 +97,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def workload_setup(name: str):
+def workload_setup(name: str, n: int = 0):
+    """Parameters of a named workload; n > 0 rescales it to n galaxies at the same density."""
     from paper_2309_08601_gb300 import synth
-    p = synth.WORKLOADS[name]
+    p = dict(synth.WORKLOADS[name])
+    if n:
+        p["side"] = p["side"] * float(np.sqrt(n / p["n"]))
+        p["n"] = int(n)
     setup = dict(n_bins=p["n_bins"], theta_min=p["theta_min"], theta_max=p["theta_max"],
                  n_max=p["n_max"])
     theta = [[t, t, t] for t in p["theta_ap"]]
@@ -148,8 +152,9 @@ def run_reference(args):
     import oracle
     from paper_2309_08601_gb300 import synth
     oracle.build_oracle()
-    p, setup, theta = workload_setup(args.workload)
-    cat = synth.workload_catalog(args.workload)
+    p, setup, theta = workload_setup(args.workload, args.n)
+    cat = synth.make_catalog(p["n"], p["side"], p["seed"], field=p["field"], weights=p["weights"],
+                             holes=p.get("holes", False))
     for _ in range(args.warmup):
         oracle_sample(cat, setup, theta, target_s=2.0, seed=99)
     tot_pairs, tot_s, cents = 0, 0.0, 0
@@ -194,7 +199,7 @@ def run_gpu(args):
         dist.barrier()
     native.lib()
 
-    p, setup, theta = workload_setup(args.workload)
+    p, setup, theta = workload_setup(args.workload, args.n)
     cat = synth.make_catalog(p["n"], p["side"], p["seed"] + 1000 * rank, field=p["field"],
                              weights=p["weights"], holes=p.get("holes", False))
     dev = api.catalog_to_device(cat)
@@ -325,6 +330,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lognormal_200k")
+    ap.add_argument("--n", type=int, default=0,
+                    help="rescale the workload to n galaxies at the same density (profiling runs)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

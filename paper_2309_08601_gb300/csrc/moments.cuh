@@ -6,10 +6,11 @@
 //  * the catalog is cell-sorted by (zbin, cell row, cell column), so the neighbours of a centre
 //    that can fall in radial bin b are a short list of contiguous index ranges, one or two per
 //    cell row crossed by the annulus [e_b, e_{b+1});
-//  * all warps stream those ranges with coalesced int2 position loads, test membership exactly
-//    on the integer squared separation, and compact the members into a shared-memory chunk
-//    (ballot + one shared atomic per warp and 32 candidates). Each member stores
-//    z = (dx + i dy)/r and its powers z^2..z^P, and w gamma_1, w gamma_2, w;
+//  * warp w streams ranges w, w + P, w + 2P, ... with coalesced int2 position loads, tests
+//    membership exactly on the integer squared separation, and compacts the members (ballot +
+//    popc) into its own region of a shared-memory chunk. Each member stores z = (dx + i dy)/r,
+//    its powers z^2..z^P, and w gamma_1, w gamma_2, w. The fixed range-to-warp assignment and
+//    the per-warp regions make the summation order, and so the result, reproducible;
 //  * the moment orders are split over the P warps of the CTA by residue: warp p owns
 //    m = p, p + P, p + 2P, ... so every warp does the same work. It walks the whole chunk,
 //    starting from z^p and multiplying by z^P (complex recurrence in registers), and keeps
@@ -61,9 +62,8 @@ struct MomSmem {
     T a[CH], b[CH], w[CH];
     int2 seg[2 * kMaxRows];  // (first sorted index, count)
     long long e2q[kMaxBins + 1];
-    int seg_next;
     int exhausted;
-    int cnt[2];
+    int cnt[8];  // members in each warp's region this round
 };
 
 // CTA barrier that may be reached from different code locations by different warps (each warp
@@ -112,6 +112,8 @@ __device__ __forceinline__ void moments_body(const MomentArgs<T>& A,
     constexpr int NAB = PL::nab(PART);
     constexpr int NABR = NAB > 0 ? NAB : 1;
     constexpr unsigned FULL = 0xffffffffu;
+    constexpr int RC = CH / P;  // region of each warp in the chunk
+    static_assert(RC >= 64, "region too small");
     const int tid = threadIdx.x, lane = tid & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int nb = A.nb, nz = A.nz, n_max = A.n_max;
@@ -136,12 +138,7 @@ __device__ __forceinline__ void moments_body(const MomentArgs<T>& A,
                 iy1 = min(iy1, A.g.ncy - 1);
                 int nrows = iy1 - iy0 + 1;
                 nrows = nrows < 0 ? 0 : (nrows > kMaxRows ? kMaxRows : nrows);
-                if (tid == 0) {
-                    s.seg_next = 0;
-                    s.exhausted = 0;
-                    s.cnt[0] = 0;
-                    s.cnt[1] = 0;
-                }
+                if (tid == 0) s.exhausted = 0;
                 for (int r = tid; r < nrows; r += NT) {
                     const int iy = iy0 + r;
                     const float ylo = (float)iy * S, yhi = ylo + S;
@@ -186,27 +183,26 @@ __device__ __forceinline__ void moments_body(const MomentArgs<T>& A,
 #pragma unroll
                 for (int j = 0; j < NW; ++j) Ww[j] = cx<T>{T(0), T(0)};
 
-                int round = 0, cur = 0, end = 0, seen = 0;
+                int kseg = PART, cur = 0, end = 0;
                 bool have = false, done = false;
                 while (true) {
-                    // ---- scan: fill the chunk until it may overflow or the ranges run out
+                    // ---- scan: fill this warp's region until it may overflow or its ranges end
+                    int mycnt = 0;
                     while (!done) {
                         if (!have) {
-                            int k = 0;
-                            if (lane == 0) k = atomicAdd(&s.seg_next, 1);
-                            k = __shfl_sync(FULL, k, 0);
-                            if (k >= n_seg) {
+                            if (kseg >= n_seg) {
                                 done = true;
                                 if (lane == 0) atomicAdd(&s.exhausted, 1);
                                 break;
                             }
-                            const int2 sg = s.seg[k];
+                            const int2 sg = s.seg[kseg];
+                            kseg += P;
                             cur = sg.x;
                             end = sg.x + sg.y;
                             have = cur < end;
                             continue;
                         }
-                        if (seen > CH - 32 * P) break;
+                        if (mycnt > RC - 32) break;
                         const int j = cur + lane;
                         bool in = false;
                         int dx = 0, dy = 0;
@@ -219,62 +215,58 @@ __device__ __forceinline__ void moments_body(const MomentArgs<T>& A,
                             in = (r2 >= lo) && (r2 < hi);
                         }
                         const unsigned m = __ballot_sync(FULL, in);
-                        if (m) {
-                            int base = 0;
-                            if (lane == 0) base = atomicAdd(&s.cnt[round & 1], __popc(m));
-                            base = __shfl_sync(FULL, base, 0);
-                            seen = base + __popc(m);
-                            if (in) {
-                                const int slot = base + __popc(m & lt_mask);
-                                const cx<T> zu = unit_vector<T>(dx, dy, r2);
-                                cx<T> zz = zu;
-                                s.zp[0][slot] = zu;
+                        if (in) {
+                            const int slot = PART * RC + mycnt + __popc(m & lt_mask);
+                            const cx<T> zu = unit_vector<T>(dx, dy, r2);
+                            cx<T> zz = zu;
+                            s.zp[0][slot] = zu;
 #pragma unroll
-                                for (int q = 1; q < P; ++q) {
-                                    zz = cmul(zz, zu);
-                                    s.zp[q][slot] = zz;
-                                }
-                                s.a[slot] = A.pa[j];
-                                s.b[slot] = A.pb[j];
-                                s.w[slot] = A.pw[j];
+                            for (int q = 1; q < P; ++q) {
+                                zz = cmul(zz, zu);
+                                s.zp[q][slot] = zz;
                             }
+                            s.a[slot] = A.pa[j];
+                            s.b[slot] = A.pb[j];
+                            s.w[slot] = A.pw[j];
                         }
+                        mycnt += __popc(m);
                         cur += 32;
                         if (cur >= end) have = false;
                     }
+                    if (lane == 0) s.cnt[PART] = mycnt;
                     cta_sync();
-                    const int n = s.cnt[round & 1];
                     const bool all_done = (s.exhausted == P);
-                    // ---- accumulate this warp's orders over the chunk
-                    for (int e = lane; e < n; e += 32) {
-                        const cx<T> zP = s.zp[P - 1][e];
-                        cx<T> zq;
-                        if constexpr (PART == 0) {
-                            zq = cx<T>{T(1), T(0)};
-                        } else {
-                            zq = s.zp[PART - 1][e];
-                        }
-                        const T av = s.a[e], bv = s.b[e], wv = s.w[e];
-#pragma unroll
-                        for (int j = 0; j < NW; ++j) {
-                            if (j < NAB) {
-                                Aa[j].x += av * zq.x;
-                                Aa[j].y += av * zq.y;
-                                Bb[j].x += bv * zq.x;
-                                Bb[j].y += bv * zq.y;
+                    // ---- accumulate this warp's orders over every region of the chunk
+                    int n = 0;
+#pragma unroll 1
+                    for (int w = 0; w < P; ++w) {
+                        const int cw = s.cnt[w];
+                        n += cw;
+                        for (int e = w * RC + lane; e < w * RC + cw; e += 32) {
+                            const cx<T> zP = s.zp[P - 1][e];
+                            cx<T> zq;
+                            if constexpr (PART == 0) {
+                                zq = cx<T>{T(1), T(0)};
+                            } else {
+                                zq = s.zp[PART - 1][e];
                             }
-                            Ww[j].x += wv * zq.x;
-                            Ww[j].y += wv * zq.y;
-                            if (j + 1 < NW) zq = cmul(zq, zP);
+                            const T av = s.a[e], bv = s.b[e], wv = s.w[e];
+#pragma unroll
+                            for (int j = 0; j < NW; ++j) {
+                                if (j < NAB) {
+                                    Aa[j].x += av * zq.x;
+                                    Aa[j].y += av * zq.y;
+                                    Bb[j].x += bv * zq.x;
+                                    Bb[j].y += bv * zq.y;
+                                }
+                                Ww[j].x += wv * zq.x;
+                                Ww[j].y += wv * zq.y;
+                                if (j + 1 < NW) zq = cmul(zq, zP);
+                            }
                         }
                     }
-                    if (tid == 0) {
-                        my_pairs += (unsigned long long)n;
-                        s.cnt[(round + 1) & 1] = 0;
-                    }
+                    if (tid == 0) my_pairs += (unsigned long long)n;
                     cta_sync();
-                    ++round;
-                    seen = 0;
                     if (all_done) break;
                 }
 
