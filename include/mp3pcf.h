@@ -96,7 +96,9 @@ mp3pcf_status mp3pcf_accumulate_moments(mp3pcf_ctx* ctx, int64_t n, const int32_
                                         const uint8_t* d_centre_mask);
 
 /* Number of centres of the last accumulate call and the number of ordered (centre, neighbour)
- * pairs it accumulated (host outputs, either may be NULL). Synchronises the stream. */
+ * pairs it accumulated (host outputs, either may be NULL). Synchronises the stream. Returns
+ * ETIMEOUT if a bounded device-side wait of the moment kernel gave up (its outputs are then
+ * invalid). */
 mp3pcf_status mp3pcf_counts(mp3pcf_ctx* ctx, int64_t* h_n_centres, int64_t* h_n_pairs);
 
 /* Copies the moments of the last accumulate call to caller device buffers, centres in

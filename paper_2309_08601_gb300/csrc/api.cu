@@ -429,7 +429,7 @@ mp3pcf_status mp3pcf_create(const mp3pcf_config* cfg, void* stream, mp3pcf_ctx**
     if (ctx->d_e2q.ensure(sizeof(long long) * (nb + 1)) != cudaSuccess ||
         ctx->d_edges.ensure(sizeof(double) * (nb + 1)) != cudaSuccess ||
         ctx->d_nodes.ensure(sizeof(double) * nb) != cudaSuccess ||
-        ctx->bb.ensure(sizeof(int) * 8) != cudaSuccess || ctx->pairs.ensure(8) != cudaSuccess ||
+        ctx->bb.ensure(sizeof(int) * 8) != cudaSuccess || ctx->pairs.ensure(16) != cudaSuccess ||
         ctx->singular.ensure(8) != cudaSuccess)
         return cleanup(MP3PCF_ENOMEM);
     if (cudaMemcpy(ctx->d_e2q.p, ctx->e2q.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -504,7 +504,7 @@ static mp3pcf_status accumulate_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq,
     cudaStream_t st = ctx->st;
     ctx->n = n;
     ctx->n_centres = 0;
-    MP3_CK(cudaMemsetAsync(ctx->pairs.p, 0, 8, st));
+    MP3_CK(cudaMemsetAsync(ctx->pairs.p, 0, 16, st));
     if (n == 0) return MP3PCF_OK;
 
     // ---- extent of the catalog (one host round trip)
@@ -645,12 +645,11 @@ mp3pcf_status mp3pcf_counts(mp3pcf_ctx* ctx, int64_t* h_n_centres, int64_t* h_n_
 {
     if (!ctx) return MP3PCF_EINVAL;
     if (h_n_centres) *h_n_centres = ctx->n_centres;
-    if (h_n_pairs) {
-        unsigned long long p = 0;
-        MP3_CK(cudaMemcpyAsync(&p, ctx->pairs.p, 8, cudaMemcpyDeviceToHost, ctx->st));
-        MP3_CK(cudaStreamSynchronize(ctx->st));
-        *h_n_pairs = (int64_t)p;
-    }
+    unsigned long long p[2] = {0, 0};
+    MP3_CK(cudaMemcpyAsync(p, ctx->pairs.p, 16, cudaMemcpyDeviceToHost, ctx->st));
+    MP3_CK(cudaStreamSynchronize(ctx->st));
+    if (h_n_pairs) *h_n_pairs = (int64_t)p[0];
+    if (p[1]) return fail(ctx, MP3PCF_ETIMEOUT, "a bounded device wait in the moment kernel gave up");
     return MP3PCF_OK;
 }
 

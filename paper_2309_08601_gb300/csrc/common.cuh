@@ -87,7 +87,7 @@ struct MomentArgs {
     const long long* e2q;       // [nb + 1] exact squared edges in fixed-point units^2
     cx<T>* G;                   // [n_centres][nz][nb][2 n_max + 3]
     cx<T>* W;                   // [n_centres][nz][nb][2 n_max + 1]
-    unsigned long long* pairs;  // pair counter
+    unsigned long long* pairs;  // [0] pair counter, [1] error flags (1: a bounded wait gave up)
 };
 
 // launchers implemented in moments_f32.cu / moments_f64.cu

@@ -2,24 +2,28 @@
 // G_m(i,b,Z) = sum_k w_k gamma_c,k e^{i m varphi_ik} and W_m(i,b,Z) = sum_k w_k e^{i m varphi_ik}
 // (paper Sec. 3.1, Eq. Gn_disc and the W_n of Eq. 3PCF_Normalization).
 //
-// Design (one CTA works on one centre at a time; persistent over centres):
+// Warp-specialised pipeline, one CTA per centre at a time (persistent over centres):
 //  * the catalog is cell-sorted by (zbin, cell row, cell column), so the neighbours of a centre
 //    that can fall in radial bin b are a short list of contiguous index ranges, one or two per
 //    cell row crossed by the annulus [e_b, e_{b+1});
-//  * warp w streams ranges w, w + P, w + 2P, ... with coalesced int2 position loads, tests
-//    membership exactly on the integer squared separation, and compacts the members (ballot +
-//    popc) into its own region of a shared-memory chunk. Each member stores z = (dx + i dy)/r,
-//    its powers z^2..z^P, and w gamma_1, w gamma_2, w. The fixed range-to-warp assignment and
-//    the per-warp regions make the summation order, and so the result, reproducible;
-//  * the moment orders are split over the P warps of the CTA by residue: warp p owns
-//    m = p, p + P, p + 2P, ... so every warp does the same work. It walks the whole chunk,
-//    starting from z^p and multiplying by z^P (complex recurrence in registers), and keeps
-//    A_m = sum w gamma_1 z^m, B_m = sum w gamma_2 z^m (m <= n_max + 3) and
-//    W_m = sum w z^m (m <= 2 n_max) in registers for the current bin;
-//  * at the end of a bin the per-lane sums are reduced across the warp and written as
-//    G_m = A_m + i B_m (m >= 0) and G_{-m} = A_m^* + i B_m^*.
-// A is kept separate from B because w gamma_c = w gamma_1 + i w gamma_2 gives both G_m and
-// G_{-m} = (sum (w gamma_c)^* z^m)^* from the same two real-weighted sums.
+//  * NS producer warps stream those ranges (producer q takes ranges q, q + NS, ...) with
+//    coalesced int2 position loads, several batches of 32 in flight, test membership exactly on
+//    the integer squared separation, and compact members (ballot + popc) into their own region
+//    of one of two shared-memory chunks. A member stores z = (dx + i dy)/r, its powers
+//    z^2..z^P, and w gamma_1, w gamma_2, w;
+//  * P consumer warps split the moment orders by residue: consumer p owns m = p, p + P, ... so
+//    all consumers do the same work. Each walks every member of a chunk, starts from z^p,
+//    multiplies by z^P (complex recurrence in registers) and accumulates
+//    A_m = sum w gamma_1 z^m, B_m = sum w gamma_2 z^m (m <= n_max + 3) and W_m = sum w z^m
+//    (m <= 2 n_max) in registers;
+//  * chunks are handed over through mbarriers (full / empty, double-buffered) whose waits are
+//    bounded by a clock budget; a wait that runs out sets an abort flag that every other wait
+//    also honours, and the kernel reports it instead of hanging;
+//  * a chunk header carries (centre, Z, bin, flags); on the last chunk of a bin the consumers
+//    reduce-scatter their per-lane sums across the warp and write G_m = A_m + i B_m,
+//    G_{-m} = A_m^* + i B_m^* and W_m.
+// The fixed range-to-producer assignment and per-producer regions make the summation order,
+// and hence the result, reproducible run to run.
 #pragma once
 
 #include "common.cuh"
@@ -30,57 +34,113 @@ template <typename T>
 struct MomTraits;
 template <>
 struct MomTraits<float> {
-    static constexpr int kPerPart = 16;  // W orders per warp
-    static constexpr int kChunk = 1024;  // members per shared chunk
+    static constexpr int kPerPart = 16;  // W orders per consumer warp (upper bound)
+    static constexpr int kChunk = 512;   // members per chunk buffer
 };
 template <>
 struct MomTraits<double> {
     static constexpr int kPerPart = 8;
-    static constexpr int kChunk = 512;
+    static constexpr int kChunk = 256;
 };
 
 template <typename T, int NMAX>
 struct MomPlan {
     static constexpr int NM = 2 * NMAX + 1;
     static constexpr int P0 = (NM + MomTraits<T>::kPerPart - 1) / MomTraits<T>::kPerPart;
-    static constexpr int P = P0 > 8 ? 8 : P0;
+    static constexpr int P = P0 > 8 ? 8 : P0;  // consumer warps
+    static constexpr int NS = 2;               // producer warps
+    static constexpr int NT = 32 * (P + NS);
     static constexpr int CH = MomTraits<T>::kChunk;
-    static constexpr int NT = 32 * P;
-    // CTAs per SM the register budget is sized for (FP32: 12 warps per SM)
-    static constexpr int MINB = sizeof(T) == 4 ? (384 / NT > 1 ? 384 / NT : 1) : 1;
-    static_assert(CH >= 64 * P, "chunk too small for the fill bound");
-    __host__ __device__ static constexpr int nw(int part) { return (2 * NMAX - part) / P + 1; }
-    __host__ __device__ static constexpr int nab(int part)
-    {
-        return part <= NMAX + 3 ? (NMAX + 3 - part) / P + 1 : 0;
-    }
+    static constexpr int RC = CH / NS;  // producer region
+    static constexpr int UNR = 4;       // candidate batches of 32 in flight per producer
+    static_assert(RC >= 32 * UNR, "region smaller than one producer step");
+    static constexpr int NWM = (2 * NMAX) / P + 1;      // W orders of consumer 0
+    static constexpr int NABM = (NMAX + 3) / P + 1;     // A, B orders of consumer 0
+    static constexpr int NA = 4 * NABM + 2 * NWM;       // scalar accumulators
+    static constexpr int NAP = (NA + 31) / 32 * 32;     // padded for the reduce-scatter
+    // CTAs per SM the register budget is sized for
+    static constexpr int MINB = sizeof(T) == 4 ? (NT <= 192 ? 3 : 2) : 1;
 };
 
 template <typename T, int P, int CH>
 struct MomSmem {
-    cx<T> zp[P][CH];  // z^1 .. z^P of each member
-    T a[CH], b[CH], w[CH];
-    int2 seg[2 * kMaxRows];  // (first sorted index, count)
+    cx<T> zp[2][P][CH];  // z^1 .. z^P of each member
+    T a[2][CH], b[2][CH], w[2][CH];
+    int cnt[2][4];   // members in each producer region
+    int hdr[2][4];   // centre row, Z, bin, flags (1: last chunk of the bin, 2: last chunk)
+    int2 seg[2 * kMaxRows];  // (first sorted index, count) of the current bin's ranges
     long long e2q[kMaxBins + 1];
-    int exhausted;
-    int cnt[8];  // members in each warp's region this round
+    unsigned long long full[2], empty[2];  // mbarriers
+    int abort;
 };
 
-// CTA barrier that may be reached from different code locations by different warps (each warp
-// runs its own specialisation of the loop nest); the non-.aligned form allows that.
-__device__ __forceinline__ void cta_sync() { asm volatile("barrier.sync 0;" ::: "memory"); }
+// ------------------------------------------------------------------ PTX helpers
 
-__device__ __forceinline__ float warp_sum(float v)
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ double warp_sum(double v)
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, int count)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, int parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase of the given parity to complete. Gives up after ~2^31 SM clocks or when
+// another wait of the CTA already gave up; then records the failure and returns false.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, int parity, volatile int* abort,
+                                          unsigned long long* err)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > (1LL << 31)) {
+            *abort = 1;
+            atomicOr(err, 1ULL);
+            return false;
+        }
+    }
+    return true;
+}
+
+// barrier among the producer warps only (named barrier 1), optionally AND-reducing a predicate
+template <int N>
+__device__ __forceinline__ void producer_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory");
+}
+
+template <int N>
+__device__ __forceinline__ bool producer_sync_and(bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.red.and.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "n"(N)
+        : "memory");
+    return r != 0;
 }
 
 template <typename T>
@@ -102,34 +162,56 @@ __device__ __forceinline__ cx<double> unit_vector<double>(int dx, int dy, long l
     return {(double)dx * inv, (double)dy * inv};
 }
 
-template <typename T, int NMAX, int PART>
-__device__ __forceinline__ void moments_body(const MomentArgs<T>& A,
-                                             MomSmem<T, MomPlan<T, NMAX>::P, MomPlan<T, NMAX>::CH>& s)
+// Reduce-scatter of N (multiple of 32) per-lane values over the warp: afterwards lane l holds
+// the warp sums of indices [l*N/32, (l+1)*N/32) in v[0 .. N/32).
+template <typename T, int N>
+__device__ __forceinline__ void warp_reduce_scatter(T (&v)[N], int lane)
+{
+#pragma unroll
+    for (int lvl = 0; lvl < 5; ++lvl) {
+        const int o = 16 >> lvl;
+        const int n = N >> lvl, half = n >> 1;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            if (i < half) {
+                const T send = up ? v[i] : v[i + half];
+                const T keep = up ? v[i + half] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ producer
+
+template <typename T, int NMAX>
+__device__ __forceinline__ void moments_producer(const MomentArgs<T>& A,
+                                                 MomSmem<T, MomPlan<T, NMAX>::P, MomPlan<T, NMAX>::CH>& s)
 {
     using PL = MomPlan<T, NMAX>;
-    constexpr int P = PL::P, CH = PL::CH, NT = PL::NT;
-    constexpr int NW = PL::nw(PART);
-    constexpr int NAB = PL::nab(PART);
-    constexpr int NABR = NAB > 0 ? NAB : 1;
+    constexpr int P = PL::P, NS = PL::NS, RC = PL::RC, UNR = PL::UNR;
+    constexpr int NPT = 32 * NS;
     constexpr unsigned FULL = 0xffffffffu;
-    constexpr int RC = CH / P;  // region of each warp in the chunk
-    static_assert(RC >= 64, "region too small");
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int q = (threadIdx.x >> 5) - P;  // producer index
+    const int lane = threadIdx.x & 31, ptid = threadIdx.x - 32 * P;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const int nb = A.nb, nz = A.nz, n_max = A.n_max;
-    const int MG = 2 * n_max + 3, MW = 2 * n_max + 1;
+    const int nb = A.nb, nz = A.nz;
     const float S = (float)A.g.side;
-    unsigned long long my_pairs = 0;
+    volatile int* abort = &s.abort;
+    int pb = 0;
+    int ph_e[2] = {0, 0};
+    bool used[2] = {false, false};
 
     for (int c = blockIdx.x; c < A.n_centres; c += gridDim.x) {
         const int ci = A.centre_idx[c];
         const int2 pc = A.pos[ci];
         const float fx = (float)((long long)pc.x - A.g.x0);
         const float fy = (float)((long long)pc.y - A.g.y0);
+        const bool last_centre = c + (int)gridDim.x >= A.n_centres;
         for (int z = 0; z < nz; ++z) {
             for (int b = 0; b < nb; ++b) {
                 const long long lo = s.e2q[b], hi = s.e2q[b + 1];
-                // ---- index ranges of the cell rows the annulus crosses (conservative)
                 const float Ro = sqrtf((float)hi) * 1.000001f + 4.0f;
                 const float Ri = fmaxf(sqrtf((float)lo) * 0.999999f - 4.0f, 0.0f);
                 int iy0 = (int)floorf((fy - Ro) / S - 0.001f);
@@ -138,8 +220,8 @@ __device__ __forceinline__ void moments_body(const MomentArgs<T>& A,
                 iy1 = min(iy1, A.g.ncy - 1);
                 int nrows = iy1 - iy0 + 1;
                 nrows = nrows < 0 ? 0 : (nrows > kMaxRows ? kMaxRows : nrows);
-                if (tid == 0) s.exhausted = 0;
-                for (int r = tid; r < nrows; r += NT) {
+                producer_sync<NPT>();  // the previous bin's ranges are no longer read
+                for (int r = ptid; r < nrows; r += NPT) {
                     const int iy = iy0 + r;
                     const float ylo = (float)iy * S, yhi = ylo + S;
                     const float dymin = fmaxf(0.0f, fmaxf(ylo - fy, fy - yhi));
@@ -174,134 +256,172 @@ __device__ __forceinline__ void moments_body(const MomentArgs<T>& A,
                     s.seg[2 * r] = s0;
                     s.seg[2 * r + 1] = s1;
                 }
-                cta_sync();
+                producer_sync<NPT>();
                 const int n_seg = 2 * nrows;
 
-                cx<T> Aa[NABR], Bb[NABR], Ww[NW];
-#pragma unroll
-                for (int j = 0; j < NABR; ++j) Aa[j] = Bb[j] = cx<T>{T(0), T(0)};
-#pragma unroll
-                for (int j = 0; j < NW; ++j) Ww[j] = cx<T>{T(0), T(0)};
-
-                int kseg = PART, cur = 0, end = 0;
+                int kseg = q, cur = 0, end = 0;
                 bool have = false, done = false;
                 while (true) {
-                    // ---- scan: fill this warp's region until it may overflow or its ranges end
+                    if (used[pb] && !*abort) {
+                        mbar_wait(&s.empty[pb], ph_e[pb], abort, A.pairs + 1);
+                        ph_e[pb] ^= 1;
+                    }
+                    used[pb] = true;
                     int mycnt = 0;
-                    while (!done) {
+                    const int base = q * RC;
+                    while (!done && !*abort) {
                         if (!have) {
                             if (kseg >= n_seg) {
                                 done = true;
-                                if (lane == 0) atomicAdd(&s.exhausted, 1);
                                 break;
                             }
                             const int2 sg = s.seg[kseg];
-                            kseg += P;
+                            kseg += NS;
                             cur = sg.x;
                             end = sg.x + sg.y;
                             have = cur < end;
                             continue;
                         }
-                        if (mycnt > RC - 32) break;
-                        const int j = cur + lane;
-                        bool in = false;
-                        int dx = 0, dy = 0;
-                        long long r2 = 0;
-                        if (j < end) {
-                            const int2 p = A.pos[j];
-                            dx = p.x - pc.x;
-                            dy = p.y - pc.y;
-                            r2 = (long long)dx * dx + (long long)dy * dy;
-                            in = (r2 >= lo) && (r2 < hi);
-                        }
-                        const unsigned m = __ballot_sync(FULL, in);
-                        if (in) {
-                            const int slot = PART * RC + mycnt + __popc(m & lt_mask);
-                            const cx<T> zu = unit_vector<T>(dx, dy, r2);
-                            cx<T> zz = zu;
-                            s.zp[0][slot] = zu;
+                        if (mycnt > RC - 32 * UNR) break;
+                        // UNR batches of 32 candidates, loads issued together
+                        int2 pp[UNR];
 #pragma unroll
-                            for (int q = 1; q < P; ++q) {
-                                zz = cmul(zz, zu);
-                                s.zp[q][slot] = zz;
-                            }
-                            s.a[slot] = A.pa[j];
-                            s.b[slot] = A.pb[j];
-                            s.w[slot] = A.pw[j];
+                        for (int u = 0; u < UNR; ++u) {
+                            const int j = cur + u * 32 + lane;
+                            pp[u] = j < end ? A.pos[j] : pc;
                         }
-                        mycnt += __popc(m);
-                        cur += 32;
+#pragma unroll
+                        for (int u = 0; u < UNR; ++u) {
+                            const int j = cur + u * 32 + lane;
+                            const int dx = pp[u].x - pc.x, dy = pp[u].y - pc.y;
+                            const long long r2 = (long long)dx * dx + (long long)dy * dy;
+                            const bool in = (j < end) && (r2 >= lo) && (r2 < hi);
+                            const unsigned m = __ballot_sync(FULL, in);
+                            if (in) {
+                                const int slot = base + mycnt + __popc(m & lt_mask);
+                                const cx<T> zu = unit_vector<T>(dx, dy, r2);
+                                cx<T> zz = zu;
+                                s.zp[pb][0][slot] = zu;
+#pragma unroll
+                                for (int k = 1; k < P; ++k) {
+                                    zz = cmul(zz, zu);
+                                    s.zp[pb][k][slot] = zz;
+                                }
+                                s.a[pb][slot] = A.pa[j];
+                                s.b[pb][slot] = A.pb[j];
+                                s.w[pb][slot] = A.pw[j];
+                            }
+                            mycnt += __popc(m);
+                        }
+                        cur += 32 * UNR;
                         if (cur >= end) have = false;
                     }
-                    if (lane == 0) s.cnt[PART] = mycnt;
-                    cta_sync();
-                    const bool all_done = (s.exhausted == P);
-                    // ---- accumulate this warp's orders over every region of the chunk
-                    int n = 0;
-#pragma unroll 1
-                    for (int w = 0; w < P; ++w) {
-                        const int cw = s.cnt[w];
-                        n += cw;
-                        for (int e = w * RC + lane; e < w * RC + cw; e += 32) {
-                            const cx<T> zP = s.zp[P - 1][e];
-                            cx<T> zq;
-                            if constexpr (PART == 0) {
-                                zq = cx<T>{T(1), T(0)};
-                            } else {
-                                zq = s.zp[PART - 1][e];
-                            }
-                            const T av = s.a[e], bv = s.b[e], wv = s.w[e];
-#pragma unroll
-                            for (int j = 0; j < NW; ++j) {
-                                if (j < NAB) {
-                                    Aa[j].x += av * zq.x;
-                                    Aa[j].y += av * zq.y;
-                                    Bb[j].x += bv * zq.x;
-                                    Bb[j].y += bv * zq.y;
-                                }
-                                Ww[j].x += wv * zq.x;
-                                Ww[j].y += wv * zq.y;
-                                if (j + 1 < NW) zq = cmul(zq, zP);
-                            }
-                        }
+                    if (*abort) done = true;
+                    if (lane == 0) s.cnt[pb][q] = mycnt;
+                    const bool all_done = producer_sync_and<NPT>(done);
+                    if (ptid == 0) {
+                        s.hdr[pb][0] = c;
+                        s.hdr[pb][1] = z;
+                        s.hdr[pb][2] = b;
+                        s.hdr[pb][3] = (all_done ? 1 : 0) |
+                                       ((all_done && last_centre && z == nz - 1 && b == nb - 1) ? 2 : 0);
                     }
-                    if (tid == 0) my_pairs += (unsigned long long)n;
-                    cta_sync();
+                    mbar_arrive(&s.full[pb]);
+                    pb ^= 1;
                     if (all_done) break;
-                }
-
-                // ---- reduce over the warp and write G, W of (centre, Z, bin)
-#pragma unroll
-                for (int j = 0; j < NW; ++j) {
-                    Ww[j].x = warp_sum(Ww[j].x);
-                    Ww[j].y = warp_sum(Ww[j].y);
-                    if (j < NAB) {
-                        Aa[j].x = warp_sum(Aa[j].x);
-                        Aa[j].y = warp_sum(Aa[j].y);
-                        Bb[j].x = warp_sum(Bb[j].x);
-                        Bb[j].y = warp_sum(Bb[j].y);
-                    }
-                }
-                if (lane == 0) {
-                    const size_t row = ((size_t)c * nz + z) * nb + b;
-                    cx<T>* Gp = A.G + row * MG;
-                    cx<T>* Wp = A.W + row * MW;
-#pragma unroll
-                    for (int j = 0; j < NW; ++j) {
-                        const int m = PART + j * P;
-                        if (m <= 2 * n_max) Wp[m] = Ww[j];
-                        if (j < NAB) {
-                            if (m <= n_max - 1)
-                                Gp[m + n_max + 3] = cx<T>{Aa[j].x - Bb[j].y, Aa[j].y + Bb[j].x};
-                            if (m >= 1 && m <= n_max + 3)
-                                Gp[n_max + 3 - m] = cx<T>{Aa[j].x + Bb[j].y, Bb[j].x - Aa[j].y};
-                        }
-                    }
                 }
             }
         }
     }
-    if (tid == 0 && my_pairs) atomicAdd(A.pairs, my_pairs);
+}
+
+// ------------------------------------------------------------------ consumer
+
+template <typename T, int NMAX>
+__device__ __forceinline__ void moments_consumer(const MomentArgs<T>& A,
+                                                 MomSmem<T, MomPlan<T, NMAX>::P, MomPlan<T, NMAX>::CH>& s,
+                                                 T* stage)
+{
+    using PL = MomPlan<T, NMAX>;
+    constexpr int P = PL::P, NS = PL::NS, RC = PL::RC;
+    constexpr int NWM = PL::NWM, NABM = PL::NABM, NAP = PL::NAP;
+    const int part = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nb = A.nb, nz = A.nz, n_max = A.n_max;
+    const int MG = 2 * n_max + 3, MW = 2 * n_max + 1;
+    // the last order slot of this consumer may fall outside the order range
+    const bool lastW = part + (NWM - 1) * P <= 2 * NMAX;
+    const bool lastAB = part + (NABM - 1) * P <= NMAX + 3;
+    const int zsel = part > 0 ? part - 1 : 0;
+    volatile int* abort = &s.abort;
+    unsigned long long my_pairs = 0;
+
+    T acc[NAP];
+#pragma unroll
+    for (int i = 0; i < NAP; ++i) acc[i] = T(0);
+
+    int cb = 0;
+    int ph_f[2] = {0, 0};
+    while (true) {
+        if (!mbar_wait(&s.full[cb], ph_f[cb], abort, A.pairs + 1)) break;
+        ph_f[cb] ^= 1;
+        const int c = s.hdr[cb][0], z = s.hdr[cb][1], b = s.hdr[cb][2], fl = s.hdr[cb][3];
+#pragma unroll 1
+        for (int qq = 0; qq < NS; ++qq) {
+            const int cnt = s.cnt[cb][qq];
+            my_pairs += (unsigned long long)cnt;
+            const int e0 = qq * RC;
+            for (int e = e0 + lane; e < e0 + cnt; e += 32) {
+                const cx<T> zP = s.zp[cb][P - 1][e];
+                cx<T> zq = s.zp[cb][zsel][e];
+                if (part == 0) zq = cx<T>{T(1), T(0)};
+                const T av = s.a[cb][e], bv = s.b[cb][e], wv = s.w[cb][e];
+#pragma unroll
+                for (int j = 0; j < NWM; ++j) {
+                    if (j < NABM) {
+                        if (j < NABM - 1 || lastAB) {
+                            acc[4 * j + 0] += av * zq.x;
+                            acc[4 * j + 1] += av * zq.y;
+                            acc[4 * j + 2] += bv * zq.x;
+                            acc[4 * j + 3] += bv * zq.y;
+                        }
+                    }
+                    if (j < NWM - 1 || lastW) {
+                        acc[4 * NABM + 2 * j + 0] += wv * zq.x;
+                        acc[4 * NABM + 2 * j + 1] += wv * zq.y;
+                    }
+                    if (j + 1 < NWM) zq = cmul(zq, zP);
+                }
+            }
+        }
+        mbar_arrive(&s.empty[cb]);
+        cb ^= 1;
+        if (fl & 1) {
+            // ---- end of (centre, Z, bin): reduce over the warp and write G, W
+            warp_reduce_scatter<T, NAP>(acc, lane);
+            constexpr int PER = NAP / 32;
+            T* st = stage + part * NAP;
+#pragma unroll
+            for (int i = 0; i < PER; ++i) st[lane * PER + i] = acc[i];
+            __syncwarp();
+            const size_t row = ((size_t)c * nz + z) * nb + b;
+            cx<T>* Gp = A.G + row * MG;
+            cx<T>* Wp = A.W + row * MW;
+            if (lane < NWM) {
+                const int j = lane, m = part + j * P;
+                if (m <= 2 * n_max) Wp[m] = cx<T>{st[4 * NABM + 2 * j], st[4 * NABM + 2 * j + 1]};
+                if (j < NABM) {
+                    const T ax = st[4 * j], ay = st[4 * j + 1], bx = st[4 * j + 2], by = st[4 * j + 3];
+                    if (m <= n_max - 1) Gp[m + n_max + 3] = cx<T>{ax - by, ay + bx};
+                    if (m >= 1 && m <= n_max + 3) Gp[n_max + 3 - m] = cx<T>{ax + by, bx - ay};
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < NAP; ++i) acc[i] = T(0);
+        }
+        if (fl & 2) break;
+    }
+    if (lane == 0 && my_pairs && part == 0) atomicAdd(A.pairs, my_pairs);
 }
 
 template <typename T, int NMAX>
@@ -310,35 +430,27 @@ __global__ void __launch_bounds__(MomPlan<T, NMAX>::NT, MomPlan<T, NMAX>::MINB) 
     using PL = MomPlan<T, NMAX>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& s = *reinterpret_cast<MomSmem<T, PL::P, PL::CH>*>(smem_raw);
+    T* stage = reinterpret_cast<T*>(smem_raw + sizeof(MomSmem<T, PL::P, PL::CH>));
     for (int i = threadIdx.x; i <= A.nb; i += blockDim.x) s.e2q[i] = A.e2q[i];
-    __syncthreads();
-    const int part = threadIdx.x >> 5;
-    // each warp runs the loop nest with its own compile-time order set; the loops are uniform
-    // across the CTA, so every warp meets the same sequence of barriers
-    switch (part) {
-#define MP3_PART(q)                                          \
-    case q:                                                  \
-        if constexpr (q < PL::P) moments_body<T, NMAX, q>(A, s); \
-        break;
-        MP3_PART(0)
-        MP3_PART(1)
-        MP3_PART(2)
-        MP3_PART(3)
-        MP3_PART(4)
-        MP3_PART(5)
-        MP3_PART(6)
-        MP3_PART(7)
-#undef MP3_PART
-        default:
-            break;
+    if (threadIdx.x == 0) {
+        mbar_init(&s.full[0], 32 * PL::NS);
+        mbar_init(&s.full[1], 32 * PL::NS);
+        mbar_init(&s.empty[0], 32 * PL::P);
+        mbar_init(&s.empty[1], 32 * PL::P);
+        s.abort = 0;
     }
+    __syncthreads();
+    if ((int)(threadIdx.x >> 5) < PL::P)
+        moments_consumer<T, NMAX>(A, s, stage);
+    else
+        moments_producer<T, NMAX>(A, s);
 }
 
 template <typename T, int NMAX>
 cudaError_t launch_moments_nmax(const MomentArgs<T>& a, int n_sm, cudaStream_t st)
 {
     using PL = MomPlan<T, NMAX>;
-    const size_t smem = sizeof(MomSmem<T, PL::P, PL::CH>);
+    const size_t smem = sizeof(MomSmem<T, PL::P, PL::CH>) + sizeof(T) * PL::P * PL::NAP;
     cudaError_t e = cudaFuncSetAttribute(moments_kernel<T, NMAX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
