@@ -220,17 +220,15 @@ __global__ void k_gather(int64_t n, const int* __restrict__ perm, const int32_t*
                          const int32_t* __restrict__ yq, const float* __restrict__ g1,
                          const float* __restrict__ g2, const float* __restrict__ w,
                          const uint8_t* __restrict__ zb, const uint8_t* __restrict__ mask,
-                         int2* __restrict__ pos, T* __restrict__ pa, T* __restrict__ pb,
-                         T* __restrict__ pw, uint8_t* __restrict__ zs, int* __restrict__ cflag)
+                         int2* __restrict__ pos, Pay<T>* __restrict__ pay,
+                         uint8_t* __restrict__ zs, int* __restrict__ cflag)
 {
     for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < n;
          d += (int64_t)gridDim.x * blockDim.x) {
         const int i = perm[d];
         pos[d] = make_int2(xq[i], yq[i]);
         const T wi = (T)w[i];
-        pa[d] = wi * (T)g1[i];
-        pb[d] = wi * (T)g2[i];
-        pw[d] = wi;
+        pay[d] = Pay<T>{wi * (T)g1[i], wi * (T)g2[i], wi, T(0)};
         zs[d] = zb ? zb[i] : 0;
         cflag[d] = mask ? (mask[i] != 0) : 1;
     }
@@ -291,7 +289,7 @@ struct mp3pcf_ctx {
     int64_t n_centres = 0;
     GridDesc grid{};
     DevBuf d_e2q, d_edges, d_nodes;
-    DevBuf bb, key, count, fill, scan_sums, scan_total, perm, pos, pa, pb, pw, zs;
+    DevBuf bb, key, count, fill, scan_sums, scan_total, perm, pos, pay, zs;
     DevBuf cflag, crank, oflag, orank, centre_idx, crow;
     DevBuf G, W, pairs, partial, singular, m3partial;
     // tracing: per-stage event pairs and kernel-launch counts
@@ -446,7 +444,7 @@ mp3pcf_status mp3pcf_destroy(mp3pcf_ctx* ctx)
     cudaStreamSynchronize(ctx->st);
     DevBuf* bufs[] = {&ctx->d_e2q, &ctx->d_edges, &ctx->d_nodes, &ctx->bb, &ctx->key,
                       &ctx->count, &ctx->fill, &ctx->scan_sums, &ctx->scan_total, &ctx->perm,
-                      &ctx->pos, &ctx->pa, &ctx->pb, &ctx->pw, &ctx->zs, &ctx->cflag,
+                      &ctx->pos, &ctx->pay, &ctx->zs, &ctx->cflag,
                       &ctx->crank, &ctx->oflag, &ctx->orank, &ctx->centre_idx, &ctx->crow,
                       &ctx->G, &ctx->W, &ctx->pairs, &ctx->partial, &ctx->singular,
                       &ctx->m3partial};
@@ -549,9 +547,7 @@ static mp3pcf_status accumulate_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq,
     MP3_CK(ctx->fill.ensure(sizeof(int) * (K + 1)));
     MP3_CK(ctx->perm.ensure(sizeof(int) * n));
     MP3_CK(ctx->pos.ensure(sizeof(int2) * n));
-    MP3_CK(ctx->pa.ensure(sizeof(T) * n));
-    MP3_CK(ctx->pb.ensure(sizeof(T) * n));
-    MP3_CK(ctx->pw.ensure(sizeof(T) * n));
+    MP3_CK(ctx->pay.ensure(sizeof(Pay<T>) * n));
     MP3_CK(ctx->zs.ensure(n));
     MP3_CK(ctx->cflag.ensure(sizeof(int) * (n + 1)));
     MP3_CK(ctx->crank.ensure(sizeof(int) * (n + 1)));
@@ -569,8 +565,8 @@ static mp3pcf_status accumulate_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq,
                                                     ctx->fill.as<int>(), ctx->perm.as<int>());
     k_cell_order<<<grid1d(K, ctx->n_sm), 256, 0, st>>>(K, ctx->count.as<int>(), ctx->perm.as<int>());
     k_gather<T><<<grid1d(n, ctx->n_sm), 256, 0, st>>>(
-        n, ctx->perm.as<int>(), xq, yq, g1, g2, w, zb, mask, ctx->pos.as<int2>(), ctx->pa.as<T>(),
-        ctx->pb.as<T>(), ctx->pw.as<T>(), ctx->zs.as<uint8_t>(), ctx->cflag.as<int>());
+        n, ctx->perm.as<int>(), xq, yq, g1, g2, w, zb, mask, ctx->pos.as<int2>(), ctx->pay.as<Pay<T>>(),
+        ctx->zs.as<uint8_t>(), ctx->cflag.as<int>());
     MP3_CK(cudaGetLastError());
 
     // ---- centre list (sorted order) and each centre's row in galaxy-index order
@@ -598,9 +594,7 @@ static mp3pcf_status accumulate_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq,
     a.n_centres = nc;
     a.centre_idx = ctx->centre_idx.as<int>();
     a.pos = ctx->pos.as<int2>();
-    a.pa = ctx->pa.as<T>();
-    a.pb = ctx->pb.as<T>();
-    a.pw = ctx->pw.as<T>();
+    a.pay = ctx->pay.as<Pay<T>>();
     a.cell_start = ctx->count.as<int>();
     a.g = g;
     a.nz = nz;
@@ -692,14 +686,14 @@ mp3pcf_status mp3pcf_contract_multipoles(mp3pcf_ctx* ctx, double* d_upsilon, dou
     ctx->launches[ST_CONTRACT] += 2;
     cudaError_t e;
     if (ctx->fp64) {
-        ContractArgs<double> a{ctx->G.as<cx<double>>(), ctx->W.as<cx<double>>(), ctx->pa.as<double>(),
-                               ctx->pb.as<double>(), ctx->pw.as<double>(), ctx->zs.as<uint8_t>(),
+        ContractArgs<double> a{ctx->G.as<cx<double>>(), ctx->W.as<cx<double>>(), ctx->pay.as<Pay<double>>(),
+                               ctx->zs.as<uint8_t>(),
                                ctx->centre_idx.as<int>(), (int32_t)nc, nz, nb, c.n_max, splits,
                                ctx->partial.as<double>()};
         e = launch_contract_f64(a, ctx->st);
     } else {
-        ContractArgs<float> a{ctx->G.as<cx<float>>(), ctx->W.as<cx<float>>(), ctx->pa.as<float>(),
-                              ctx->pb.as<float>(), ctx->pw.as<float>(), ctx->zs.as<uint8_t>(),
+        ContractArgs<float> a{ctx->G.as<cx<float>>(), ctx->W.as<cx<float>>(), ctx->pay.as<Pay<float>>(),
+                              ctx->zs.as<uint8_t>(),
                               ctx->centre_idx.as<int>(), (int32_t)nc, nz, nb, c.n_max, splits,
                               ctx->partial.as<double>()};
         e = launch_contract_f32(a, ctx->st);

@@ -62,6 +62,12 @@ __host__ __device__ __forceinline__ cx<double> cdiv(cx<double> a, cx<double> b)
     return {(a.x * bx + a.y * by) / (d * s), (a.y * bx - a.x * by) / (d * s)};
 }
 
+// per-galaxy payload in sorted order, one aligned record: w gamma_1, w gamma_2, w
+template <typename T>
+struct alignas(4 * sizeof(T)) Pay {
+    T a, b, w, pad;
+};
+
 // ------------------------------------------------------------------ geometry of the cell grid
 
 struct GridDesc {
@@ -78,9 +84,7 @@ struct MomentArgs {
     int32_t n_centres;
     const int32_t* centre_idx;  // sorted position of each centre
     const int2* pos;            // sorted fixed-point positions
-    const T* pa;                // sorted w * gamma_1
-    const T* pb;                // sorted w * gamma_2
-    const T* pw;                // sorted w
+    const Pay<T>* pay;          // sorted (w gamma_1, w gamma_2, w)
     const int32_t* cell_start;  // [n_z * ncells + 1], key = zbin * ncells + cy * ncx + cx
     GridDesc g;
     int32_t nz, nb, n_max;
@@ -100,9 +104,7 @@ template <typename T>
 struct ContractArgs {
     const cx<T>* G;
     const cx<T>* W;
-    const T* pa;               // sorted w gamma_1
-    const T* pb;               // sorted w gamma_2
-    const T* pw;               // sorted w
+    const Pay<T>* pay;         // sorted (w gamma_1, w gamma_2, w)
     const uint8_t* zs;         // sorted zbin
     const int32_t* centre_idx; // sorted position of each centre (row order of G, W)
     int32_t n_centres;

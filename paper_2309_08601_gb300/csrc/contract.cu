@@ -64,13 +64,14 @@ __global__ void __launch_bounds__(kThreads) contract_kernel(const ContractArgs<T
                 const int d = a.centre_idx[c];
                 const int zc = a.zs ? (int)a.zs[d] : 0;
                 if (zc == z1) {
+                    const Pay<T> pv = a.pay[d];
                     cx<T> coef;
                     if (kind == 4) {
-                        coef = cx<T>{a.pw[d], T(0)};
+                        coef = cx<T>{pv.w, T(0)};
                     } else if (kind == 1) {
-                        coef = cx<T>{-a.pa[d], a.pb[d]};  // -(w gamma)^*
+                        coef = cx<T>{-pv.a, pv.b};  // -(w gamma)^*
                     } else {
-                        coef = cx<T>{-a.pa[d], -a.pb[d]};  // -(w gamma)
+                        coef = cx<T>{-pv.a, -pv.b};  // -(w gamma)
                     }
                     X = src[(((size_t)c * nz + z2) * nb + b) * M + mx + off];
                     Y = src[(((size_t)c * nz + z3) * nb + b) * M + my + off];

@@ -7,7 +7,8 @@
 //    that can fall in radial bin b are a short list of contiguous index ranges, one or two per
 //    cell row crossed by the annulus [e_b, e_{b+1});
 //  * NS producer warps stream those ranges (producer q takes ranges q, q + NS, ...) with
-//    coalesced int2 position loads, several batches of 32 in flight, test membership exactly on
+//    coalesced loads of positions and payload records, several batches of 32 in flight (all
+//    loads of a step are issued before any is used), test membership exactly on
 //    the integer squared separation, and compact members (ballot + popc) into their own region
 //    of one of two shared-memory chunks. A member stores z = (dx + i dy)/r, its powers
 //    z^2..z^P, and w gamma_1, w gamma_2, w;
@@ -285,10 +286,17 @@ __device__ __forceinline__ void moments_producer(const MomentArgs<T>& A,
                         if (mycnt > RC - 32 * UNR) break;
                         // UNR batches of 32 candidates, loads issued together
                         int2 pp[UNR];
+                        Pay<T> py[UNR];
 #pragma unroll
                         for (int u = 0; u < UNR; ++u) {
                             const int j = cur + u * 32 + lane;
-                            pp[u] = j < end ? A.pos[j] : pc;
+                            if (j < end) {
+                                pp[u] = A.pos[j];
+                                py[u] = A.pay[j];
+                            } else {
+                                pp[u] = pc;
+                                py[u] = Pay<T>{T(0), T(0), T(0), T(0)};
+                            }
                         }
 #pragma unroll
                         for (int u = 0; u < UNR; ++u) {
@@ -307,9 +315,9 @@ __device__ __forceinline__ void moments_producer(const MomentArgs<T>& A,
                                     zz = cmul(zz, zu);
                                     s.zp[pb][k][slot] = zz;
                                 }
-                                s.a[pb][slot] = A.pa[j];
-                                s.b[pb][slot] = A.pb[j];
-                                s.w[pb][slot] = A.pw[j];
+                                s.a[pb][slot] = py[u].a;
+                                s.b[pb][slot] = py[u].b;
+                                s.w[pb][slot] = py[u].w;
                             }
                             mycnt += __popc(m);
                         }
