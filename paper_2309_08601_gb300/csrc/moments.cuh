@@ -6,7 +6,8 @@
 //  * the catalog is cell-sorted by (zbin, cell row, cell column), so the neighbours of a centre
 //    that can fall in radial bin b are a short list of contiguous index ranges, one or two per
 //    cell row crossed by the annulus [e_b, e_{b+1});
-//  * NS producer warps stream those ranges (producer q takes ranges q, q + NS, ...) with
+//  * the ranges of a bin are concatenated into one flat candidate stream (prefix sums of their
+//    lengths) that is split evenly between NS producer warps; each streams its share with
 //    coalesced loads of positions and payload records, several batches of 32 in flight (all
 //    loads of a step are issued before any is used), test membership exactly on
 //    the integer squared separation, and compact members (ballot + popc) into their own region
@@ -29,6 +30,26 @@
 
 #include "common.cuh"
 
+// Pipeline parameters (compile-time; the defaults are the tuned values).
+#ifndef MP3_MOM_NS
+#define MP3_MOM_NS 2  // producer warps
+#endif
+#ifndef MP3_MOM_UNR
+#define MP3_MOM_UNR 4  // candidate batches of 32 a producer loads before using any
+#endif
+#ifndef MP3_MOM_CHUNK_F32
+#define MP3_MOM_CHUNK_F32 512  // members per chunk buffer (FP32)
+#endif
+#ifndef MP3_MOM_MINB_F32
+#define MP3_MOM_MINB_F32 3  // CTAs per SM the FP32 register budget is sized for
+#endif
+#ifndef MP3_MOM_WAIT_NS
+#define MP3_MOM_WAIT_NS 0  // suspend-time hint (ns) of the producers' waits for a free buffer
+#endif
+#ifndef MP3_MOM_CWAIT_NS
+#define MP3_MOM_CWAIT_NS 0  // suspend-time hint (ns) of the consumers' waits for a full buffer
+#endif
+
 namespace mp3 {
 
 template <typename T>
@@ -36,7 +57,7 @@ struct MomTraits;
 template <>
 struct MomTraits<float> {
     static constexpr int kPerPart = 16;  // W orders per consumer warp (upper bound)
-    static constexpr int kChunk = 512;   // members per chunk buffer
+    static constexpr int kChunk = MP3_MOM_CHUNK_F32;  // members per chunk buffer
 };
 template <>
 struct MomTraits<double> {
@@ -49,27 +70,30 @@ struct MomPlan {
     static constexpr int NM = 2 * NMAX + 1;
     static constexpr int P0 = (NM + MomTraits<T>::kPerPart - 1) / MomTraits<T>::kPerPart;
     static constexpr int P = P0 > 8 ? 8 : P0;  // consumer warps
-    static constexpr int NS = 2;               // producer warps
+    static constexpr int NS = sizeof(T) == 4 ? MP3_MOM_NS : 2;  // producer warps
     static constexpr int NT = 32 * (P + NS);
     static constexpr int CH = MomTraits<T>::kChunk;
     static constexpr int RC = CH / NS;  // producer region
-    static constexpr int UNR = 4;       // candidate batches of 32 in flight per producer
+    static constexpr int UNR = MP3_MOM_UNR;  // candidate batches of 32 in flight per producer
     static_assert(RC >= 32 * UNR, "region smaller than one producer step");
     static constexpr int NWM = (2 * NMAX) / P + 1;      // W orders of consumer 0
     static constexpr int NABM = (NMAX + 3) / P + 1;     // A, B orders of consumer 0
     static constexpr int NA = 4 * NABM + 2 * NWM;       // scalar accumulators
     static constexpr int NAP = (NA + 31) / 32 * 32;     // padded for the reduce-scatter
     // CTAs per SM the register budget is sized for
-    static constexpr int MINB = sizeof(T) == 4 ? (NT <= 192 ? 3 : 2) : 1;
+    static constexpr int MINB_R = 65536 / (NT * 96) > 0 ? 65536 / (NT * 96) : 1;
+    static constexpr int MINB = sizeof(T) == 4 ? (MP3_MOM_MINB_F32 < MINB_R ? MP3_MOM_MINB_F32 : MINB_R) : 1;
 };
 
 template <typename T, int P, int CH>
 struct MomSmem {
     cx<T> zp[2][P][CH];  // z^1 .. z^P of each member
     T a[2][CH], b[2][CH], w[2][CH];
-    int cnt[2][4];   // members in each producer region
+    int cnt[2][8];   // members in each producer region
     int hdr[2][4];   // centre row, Z, bin, flags (1: last chunk of the bin, 2: last chunk)
     int2 seg[2 * kMaxRows];  // (first sorted index, count) of the current bin's ranges
+    int pre[2 * kMaxRows + 1];  // exclusive prefix sums of the range lengths
+    int wtot[8];                // per-producer-warp partial sums of the prefix scan
     long long e2q[kMaxBins + 1];
     unsigned long long full[2], empty[2];  // mbarriers
     int abort;
@@ -105,13 +129,27 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, int parit
     return ok != 0;
 }
 
+__device__ __forceinline__ bool mbar_try_wait_hint(unsigned long long* bar, int parity, uint32_t ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Waits for the phase of the given parity to complete. Gives up after ~2^31 SM clocks or when
 // another wait of the CTA already gave up; then records the failure and returns false.
+template <int HINT_NS>
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, int parity, volatile int* abort,
                                           unsigned long long* err)
 {
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
+    while (!(HINT_NS > 0 ? mbar_try_wait_hint(bar, parity, HINT_NS) : mbar_try_wait(bar, parity))) {
         if (*abort) return false;
         if (clock64() - t0 > (1LL << 31)) {
             *abort = 1;
@@ -150,7 +188,11 @@ __device__ __forceinline__ cx<T> unit_vector(int dx, int dy, long long r2);
 template <>
 __device__ __forceinline__ cx<float> unit_vector<float>(int dx, int dy, long long r2)
 {
-    const float rf = (float)r2;
+    // |dx|, |dy| < 2^24 are exact in FP32; r^2 here only normalises z (the bin test used the
+    // exact integer r2)
+    (void)r2;
+    const float fdx = (float)dx, fdy = (float)dy;
+    const float rf = fdx * fdx + fdy * fdy;
     float inv = rsqrtf(rf);
     inv = inv * (1.5f - 0.5f * rf * inv * inv);  // one Newton step
     return {(float)dx * inv, (float)dy * inv};
@@ -199,6 +241,7 @@ __device__ __forceinline__ void moments_producer(const MomentArgs<T>& A,
     const unsigned lt_mask = (1u << lane) - 1u;
     const int nb = A.nb, nz = A.nz;
     const float S = (float)A.g.side;
+    const float iS = 1.0f / S;
     volatile int* abort = &s.abort;
     int pb = 0;
     int ph_e[2] = {0, 0};
@@ -215,8 +258,8 @@ __device__ __forceinline__ void moments_producer(const MomentArgs<T>& A,
                 const long long lo = s.e2q[b], hi = s.e2q[b + 1];
                 const float Ro = sqrtf((float)hi) * 1.000001f + 4.0f;
                 const float Ri = fmaxf(sqrtf((float)lo) * 0.999999f - 4.0f, 0.0f);
-                int iy0 = (int)floorf((fy - Ro) / S - 0.001f);
-                int iy1 = (int)floorf((fy + Ro) / S + 0.001f);
+                int iy0 = (int)floorf((fy - Ro) * iS - 0.001f);
+                int iy1 = (int)floorf((fy + Ro) * iS + 0.001f);
                 iy0 = max(iy0, 0);
                 iy1 = min(iy1, A.g.ncy - 1);
                 int nrows = iy1 - iy0 + 1;
@@ -231,16 +274,16 @@ __device__ __forceinline__ void moments_producer(const MomentArgs<T>& A,
                     const float ho2 = Ro * Ro - dymin * dymin + 1e-6f * Ro * Ro;
                     if (ho2 > 0.0f) {
                         const float hx = sqrtf(ho2);
-                        const int ix0 = max((int)floorf((fx - hx) / S - 0.001f), 0);
-                        const int ix1 = min((int)floorf((fx + hx) / S + 0.001f), A.g.ncx - 1);
+                        const int ix0 = max((int)floorf((fx - hx) * iS - 0.001f), 0);
+                        const int ix1 = min((int)floorf((fx + hx) * iS + 0.001f), A.g.ncx - 1);
                         if (ix0 <= ix1) {
                             int h0 = 1, h1 = 0;
                             const float hi2 = Ri * Ri - dymax * dymax - 1e-6f * Ri * Ri;
                             if (hi2 > 0.0f) {
                                 const float hin = sqrtf(hi2) - 2.0f;
                                 if (hin > 0.0f) {
-                                    h0 = (int)ceilf((fx - hin) / S + 0.001f);
-                                    h1 = (int)floorf((fx + hin) / S - 0.001f) - 1;
+                                    h0 = (int)ceilf((fx - hin) * iS + 0.001f);
+                                    h1 = (int)floorf((fx + hin) * iS - 0.001f) - 1;
                                 }
                             }
                             const int* cs = A.cell_start + (size_t)z * A.g.ncells + (size_t)iy * A.g.ncx;
@@ -259,38 +302,69 @@ __device__ __forceinline__ void moments_producer(const MomentArgs<T>& A,
                 }
                 producer_sync<NPT>();
                 const int n_seg = 2 * nrows;
-
-                int kseg = q, cur = 0, end = 0;
-                bool have = false, done = false;
+                // ---- prefix sums of the range lengths: the ranges form one flat candidate
+                //      stream, split evenly between the producer warps
+                {
+                    const int blk = (n_seg + NPT - 1) / NPT;
+                    const int k0 = ptid * blk, k1 = min(k0 + blk, n_seg);
+                    int loc = 0;
+                    for (int k = k0; k < k1; ++k) loc += s.seg[k].y;
+                    int incl = loc;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(FULL, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    if (lane == 31) s.wtot[q] = incl;
+                    producer_sync<NPT>();
+                    int run = incl - loc, tot = 0;
+                    for (int w = 0; w < NS; ++w) {
+                        if (w < q) run += s.wtot[w];
+                        tot += s.wtot[w];
+                    }
+                    for (int k = k0; k < k1; ++k) {
+                        s.pre[k] = run;
+                        run += s.seg[k].y;
+                    }
+                    if (ptid == 0) s.pre[n_seg] = tot;
+                }
+                producer_sync<NPT>();
+                const int total = s.pre[n_seg];
+                const int tq0 = (int)((long long)total * q / NS), tq1 = (int)((long long)total * (q + 1) / NS);
+                // each lane walks the ranges: ks = range holding flat candidate t
+                int tb = tq0;  // first flat candidate of the next step
+                int ks = 0;
+                {
+                    int lo_k = 0, hi_k = n_seg;  // largest k with pre[k] <= tq0 + lane
+                    const int t = tq0 + lane;
+                    while (hi_k - lo_k > 1) {
+                        const int mid = (lo_k + hi_k) >> 1;
+                        if (s.pre[mid] <= t) lo_k = mid; else hi_k = mid;
+                    }
+                    ks = lo_k;
+                }
+                bool done = tb >= tq1;
                 while (true) {
                     if (used[pb] && !*abort) {
-                        mbar_wait(&s.empty[pb], ph_e[pb], abort, A.pairs + 1);
+                        mbar_wait<MP3_MOM_WAIT_NS>(&s.empty[pb], ph_e[pb], abort, A.pairs + 1);
                         ph_e[pb] ^= 1;
                     }
                     used[pb] = true;
                     int mycnt = 0;
                     const int base = q * RC;
                     while (!done && !*abort) {
-                        if (!have) {
-                            if (kseg >= n_seg) {
-                                done = true;
-                                break;
-                            }
-                            const int2 sg = s.seg[kseg];
-                            kseg += NS;
-                            cur = sg.x;
-                            end = sg.x + sg.y;
-                            have = cur < end;
-                            continue;
-                        }
                         if (mycnt > RC - 32 * UNR) break;
-                        // UNR batches of 32 candidates, loads issued together
+                        // UNR batches of 32 flat candidates, all loads issued before any use
                         int2 pp[UNR];
                         Pay<T> py[UNR];
+                        bool ok[UNR];
 #pragma unroll
                         for (int u = 0; u < UNR; ++u) {
-                            const int j = cur + u * 32 + lane;
-                            if (j < end) {
+                            const int t = tb + u * 32 + lane;
+                            ok[u] = t < tq1;
+                            while (ks + 1 < n_seg && s.pre[ks + 1] <= t) ++ks;
+                            const int j = s.seg[ks].x + (t - s.pre[ks]);
+                            if (ok[u]) {
                                 pp[u] = A.pos[j];
                                 py[u] = A.pay[j];
                             } else {
@@ -300,10 +374,9 @@ __device__ __forceinline__ void moments_producer(const MomentArgs<T>& A,
                         }
 #pragma unroll
                         for (int u = 0; u < UNR; ++u) {
-                            const int j = cur + u * 32 + lane;
                             const int dx = pp[u].x - pc.x, dy = pp[u].y - pc.y;
                             const long long r2 = (long long)dx * dx + (long long)dy * dy;
-                            const bool in = (j < end) && (r2 >= lo) && (r2 < hi);
+                            const bool in = ok[u] && (r2 >= lo) && (r2 < hi);
                             const unsigned m = __ballot_sync(FULL, in);
                             if (in) {
                                 const int slot = base + mycnt + __popc(m & lt_mask);
@@ -321,8 +394,8 @@ __device__ __forceinline__ void moments_producer(const MomentArgs<T>& A,
                             }
                             mycnt += __popc(m);
                         }
-                        cur += 32 * UNR;
-                        if (cur >= end) have = false;
+                        tb += 32 * UNR;
+                        if (tb >= tq1) done = true;
                     }
                     if (*abort) done = true;
                     if (lane == 0) s.cnt[pb][q] = mycnt;
@@ -370,7 +443,7 @@ __device__ __forceinline__ void moments_consumer(const MomentArgs<T>& A,
     int cb = 0;
     int ph_f[2] = {0, 0};
     while (true) {
-        if (!mbar_wait(&s.full[cb], ph_f[cb], abort, A.pairs + 1)) break;
+        if (!mbar_wait<MP3_MOM_CWAIT_NS>(&s.full[cb], ph_f[cb], abort, A.pairs + 1)) break;
         ph_f[cb] ^= 1;
         const int c = s.hdr[cb][0], z = s.hdr[cb][1], b = s.hdr[cb][2], fl = s.hdr[cb][3];
 #pragma unroll 1
