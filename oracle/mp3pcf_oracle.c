@@ -68,7 +68,7 @@ static int cfg_ok(const orc_cfg* c)
 
 static inline int nz3(const orc_cfg* c) { return c->n_z * c->n_z * c->n_z; }
 
-/* ---- radial bins (Sec. 2.3: bins Theta_i = [Theta_low, Theta_up]; half-open reading) ---- */
+/* ---- radial bins (Sec. 2.4: bins Theta_i = [Theta_low, Theta_up]; half-open reading) ---- */
 
 int orc_edges(const orc_cfg* c, double* e, int64_t* e2q)
 {
@@ -416,7 +416,7 @@ int orc_edge_correct(const orc_cfg* c, const double* ups_in, const double* norm_
     return nsing ? ORC_ESINGULAR : ORC_OK;
 }
 
-/* ---- multipoles -> Gamma^x(phi) -> Gamma^cen (Sec. 2.2, Eqs. X2Centroid0-3 with the
+/* ---- multipoles -> Gamma^x(phi) -> Gamma^cen (Sec. 2.3, Eqs. X2Centroid0-3 with the
  *      phi_1-free rotation factors printed below them) ---- */
 
 /* factor turning Gamma^x_mu(t1, t2, phi) into Gamma^cen_mu */
@@ -628,7 +628,7 @@ int orc_to_map3(const orc_cfg* c, const double* gcen_in, int64_t n_ap, const dou
     return ORC_OK;
 }
 
-/* ---- brute-force triplet sums straight from the definitions (Sec. 2.2, Eqs. Gamma0_def -
+/* ---- brute-force triplet sums straight from the definitions (Sec. 2.2 Eqs. Gamma0_def -
  *      Gamma3_def in the x-projection Eq. xprojection; Eqs. TripletUpsilon and TripletNorm):
  *      for every ordered triplet (i, j, k) with theta_ij in bin b1 and theta_ik in bin b2
  *      (j = k included), phi = varphi_ik - varphi_ij,

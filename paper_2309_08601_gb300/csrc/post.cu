@@ -1,5 +1,5 @@
 // FP64 stages after the contraction: the edge-correction solve (paper Sec. 3.4), the multipole
-// sum to Gamma^x(phi) and its conversion to the centroid projection (Sec. 2.2, Sec. 4), and the
+// sum to Gamma^x(phi) and its conversion to the centroid projection (Sec. 2.3, Sec. 4), and the
 // aperture-measure integrals (Sec. 5.2, App. C).
 #include <math.h>
 

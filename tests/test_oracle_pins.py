@@ -20,7 +20,7 @@ def _cat_from_int(xq, yq, g, w):
                    g.imag.astype(np.float32), np.asarray(w, np.float32), None, 0.0, QUANTUM)
 
 
-# ---------------------------------------------------------------- bins (Sec. 2.3, reading R3)
+# ---------------------------------------------------------------- bins (Sec. 2.4, half-open reading)
 
 def test_bin_edges_are_log_spaced_and_half_open(orc):
     s = orc.Setup(n_bins=5, theta_min=1.0, theta_max=10.0, n_max=2)
