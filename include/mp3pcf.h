@@ -74,7 +74,7 @@ mp3pcf_status mp3pcf_destroy(mp3pcf_ctx* ctx);
 const char* mp3pcf_last_error(const mp3pcf_ctx* ctx);
 
 /* Host-only, no CUDA call: the bin edges e_b (arcmin, n_bins+1 values) and the exact integer
- * squared edges ceil((e_b/quantum)^2) (n_bins+1 values) the pair test uses (Sec. 2.3; the
+ * squared edges ceil((e_b/quantum)^2) (n_bins+1 values) the pair test uses (Sec. 2.4; the
  * half-open reading of the bin interval). Either output may be NULL. */
 mp3pcf_status mp3pcf_bin_edges(const mp3pcf_config* cfg, double* h_edges, int64_t* h_edges2_q);
 
@@ -133,7 +133,7 @@ mp3pcf_status mp3pcf_edge_correct(mp3pcf_ctx* ctx, const double* d_upsilon, cons
 
 /* Gamma^x_mu(b1, b2, phi_k) = sum_n Gamma_{mu,n} e^{i n phi_k}, phi_k = (k+1/2) 2 pi / n_phi
  * (Sec. 4: linear angular bins on [0, 2 pi]); projection 1 multiplies by the rotation factors
- * of Eqs. X2Centroid0-3 (Sec. 2.2) evaluated at the radial nodes of b1 and b2, giving the
+ * of Eqs. X2Centroid0-3 (Sec. 2.3) evaluated at the radial nodes of b1 and b2, giving the
  * centroid projection. Output d_gamma_phi [n_z^3][4][n_bins][n_bins][n_phi] complex double. */
 mp3pcf_status mp3pcf_to_gamma(mp3pcf_ctx* ctx, const double* d_gamma_n, int32_t projection,
                               double* d_gamma_phi);
@@ -158,6 +158,23 @@ mp3pcf_status mp3pcf_to_map3(mp3pcf_ctx* ctx, const double* d_gamma_cen, int64_t
  * reset != 0 clears the counters after reading. Synchronises the stream. */
 mp3pcf_status mp3pcf_set_timing(mp3pcf_ctx* ctx, int32_t on);
 mp3pcf_status mp3pcf_stage_times(mp3pcf_ctx* ctx, double* h_ms, int64_t* h_launches, int32_t reset);
+
+/* Allocation-free form of mp3pcf_to_map3 (the paper has no counterpart: it is a service of this
+ * library). For callers that may not allocate device memory, e.g. a plugin inside a host
+ * application that owns all device memory through its own pool, or a service held to a fixed
+ * memory budget: no context is needed and nothing is allocated. Same inputs and outputs as
+ * mp3pcf_to_map3 (cfg as for mp3pcf_create; d_gamma_cen from mp3pcf_to_gamma with projection 1),
+ * enqueued on `stream` (cudaStream_t, NULL: legacy default stream).
+ * Scratch: one static 1 MiB device array inside the library, held by every GPU that loads the
+ * library until the process exits. It limits n_z^3 * n_ap to at most 255; larger requests
+ * return EINVAL and enqueue nothing. Every call shares that array: calls whose work overlaps on
+ * the GPU (two streams, or two host threads on one device) race and must be ordered by the
+ * caller. The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Returns EINVAL for a bad configuration or argument, ECUDA if a CUDA call fails. */
+mp3pcf_status mp3pcf_to_map3_noalloc(const mp3pcf_config* cfg, void* stream,
+                                     const double* d_gamma_cen, int64_t n_ap,
+                                     const double* d_theta_ap, double* d_corr, double* d_m8);
 
 #ifdef __cplusplus
 }
