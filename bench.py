@@ -30,6 +30,11 @@ METRIC = "neighbour-pair harmonic accumulations/s; catalogs/s vs FP64 GPU path a
 UNIT = "pair-accumulations/s"
 PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (derived; FP32 FMA pipe)"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
+# DRAM bytes (read + write) per launch of the current moments kernel at the lognormal_200k
+# workload: ncu capture at 50 000 galaxies (profiles/moments_kernel_lognormal_50k.md) scaled to
+# 200 000 centres (the traffic is the G/W write, proportional to the number of centres).
+# Set to None whenever the kernel changes until it is captured again.
+MOMENTS_TRAFFIC_BYTES = 4 * (12.030976e6 + 934.902784e6)
 
 
 def flops_per_pair(n_max: int) -> int:
@@ -250,7 +255,11 @@ def run_gpu(args):
     achieved = fpp * pairs / (k1_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": "moments_kernel<float,30>", "achieved": achieved,
                 "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                "traffic": args.k1_traffic, "flops_per_pair": fpp, "pairs_per_launch": pairs,
+                "traffic": (args.k1_traffic if args.k1_traffic is not None else
+                            (MOMENTS_TRAFFIC_BYTES if (args.workload == "lognormal_200k" and not args.n
+                                                       and args.precision == "fp32") else None)),
+                "traffic_note": "ncu DRAM read+write, capture at 50 000 galaxies scaled by centres",
+                "flops_per_pair": fpp, "pairs_per_launch": pairs,
                 "launch_ms": k1_ms, "peak_source": PEAK_NOTE}
     launches = sum(v[1] for v in stages.values())
 
@@ -338,7 +347,8 @@ def main(argv=None):
     ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work sampled")
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     ap.add_argument("--k1-traffic", type=float, default=None,
-                    help="DRAM bytes per moments launch from the committed ncu summary")
+                    help="DRAM bytes per moments launch (default: the committed ncu figure, at "
+                         "the lognormal_200k workload only)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
