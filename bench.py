@@ -133,13 +133,14 @@ def oracle_sample(cat, setup, theta, target_s: float, seed: int = 0):
     rng = np.random.default_rng(seed)
     order = rng.permutation(cat.n)
     # calibrate on a few centres, then size the sample
-    probe = np.sort(order[:8])
+    nprobe = 4 * oracle.num_threads()
+    probe = np.sort(order[:nprobe])
     t0 = time.perf_counter()
     pp = oracle.count_pairs(s, cat, probe)
     G, W = oracle.moments(s, cat, probe)
     oracle.contract(s, cat, G, W, probe)
     dt = max(time.perf_counter() - t0, 1e-3)
-    per_centre = dt / 8
+    per_centre = dt / nprobe
     k = int(np.clip(target_s / per_centre, 8, cat.n))
     cen = np.sort(order[:k])
     pairs = oracle.count_pairs(s, cat, cen)
