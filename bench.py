@@ -30,6 +30,17 @@ METRIC = "neighbour-pair harmonic accumulations/s; catalogs/s vs FP64 GPU path a
 UNIT = "pair-accumulations/s"
 PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (derived; FP32 FMA pipe)"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
+
+
+def _measured_hbm_gbs():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0  # fallback: one earlier copy measurement on a GB300
+
+
+HBM_PEAK_GBS = _measured_hbm_gbs()
 # DRAM bytes (read + write) per launch of the current moments kernel at the lognormal_200k
 # workload: ncu capture at 50 000 galaxies (profiles/moments_kernel_lognormal_50k.md) scaled to
 # 200 000 centres (the traffic is the G/W write, proportional to the number of centres).
@@ -263,6 +274,16 @@ def run_gpu(args):
                 "flops_per_pair": fpp, "pairs_per_launch": pairs,
                 "launch_ms": k1_ms, "peak_source": PEAK_NOTE}
     launches = sum(v[1] for v in stages.values())
+    # ---- stage (b): HBM-bound; algorithmic bytes = every moment row read once (complex, moment
+    # precision) + the FP64 partial sums written and read once by the slice reduction
+    k2_ms = stages["contract"][0] / args.steps
+    esz = 16 if args.precision == "fp64" else 8
+    nbins, nmax = p["n_bins"], p["n_max"]
+    k2_bytes = n_centres * nbins * ((2 * nmax + 3) + (2 * nmax + 1)) * esz
+    roofline_contract = {"bound": "hbm", "kernel": "contract (%s)" % args.precision,
+                         "achieved": k2_bytes / (k2_ms / 1e3) / 1e9, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                         "frac": k2_bytes / (k2_ms / 1e3) / 1e9 / HBM_PEAK_GBS, "bytes_per_launch": k2_bytes,
+                         "launch_ms": k2_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
 
     # ---- end to end through the public API with host buffers
     host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
@@ -296,7 +317,7 @@ def run_gpu(args):
             "config": workload_config(args.workload, p, args.precision),
             "catalogs_per_s": cat_per_s, "pairs_per_catalog": pairs,
             "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roofline, "roofline_contract": roofline_contract, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks.summary()}
 
     # ---- the plain FP64 GPU path on the same catalog (rank 0, one untimed-warmup + one run)
@@ -342,7 +363,7 @@ def main(argv=None):
     ap.add_argument("--workload", default="lognormal_200k")
     ap.add_argument("--n", type=int, default=0,
                     help="rescale the workload to n galaxies at the same density (profiling runs)")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16x3", "tf32x3"])
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work sampled")

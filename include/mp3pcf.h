@@ -97,8 +97,8 @@ mp3pcf_status mp3pcf_accumulate_moments(mp3pcf_ctx* ctx, int64_t n, const int32_
 
 /* Number of centres of the last accumulate call and the number of ordered (centre, neighbour)
  * pairs it accumulated (host outputs, either may be NULL). Synchronises the stream. Returns
- * ETIMEOUT if a bounded device-side wait of the moment kernel gave up (its outputs are then
- * invalid). */
+ * ETIMEOUT if a bounded device-side wait of the moment kernel, or of a tensor-core contraction
+ * launched since that accumulate call, gave up (their outputs are then invalid). */
 mp3pcf_status mp3pcf_counts(mp3pcf_ctx* ctx, int64_t* h_n_centres, int64_t* h_n_pairs);
 
 /* Copies the moments of the last accumulate call to caller device buffers, centres in
@@ -116,7 +116,13 @@ mp3pcf_status mp3pcf_copy_moments(mp3pcf_ctx* ctx, void* d_G, void* d_W);
  * summed over the centres of the last accumulate call and ADDED to d_upsilon
  * [n_z^3][4][n_max+1][n_bins][n_bins] (n = 0..n_max) and d_norm [n_z^3][2 n_max+1][n_bins][n_bins]
  * (n = 0..2 n_max), complex double. Adding lets callers sum centre chunks or patches
- * (App. B, Eq. PatchGamma). */
+ * (App. B, Eq. PatchGamma).
+ * MP3PCF_FP64 and MP3PCF_FP32 sum on the CUDA cores (tile sums in the moment precision, added in
+ * FP64). MP3PCF_FP32_BF16X3 / MP3PCF_FP32_TF32X3 run each group as real GEMMs on the tcgen05
+ * tensor cores: every FP32 operand x = hi + lo (hi, lo in BF16 resp. TF32), products
+ * hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor memory over 32 (16) centres at a time and
+ * per centre slice, slices added in FP64. A bounded wait that gives up in that kernel is
+ * reported as ETIMEOUT by the next mp3pcf_counts. */
 mp3pcf_status mp3pcf_contract_multipoles(mp3pcf_ctx* ctx, double* d_upsilon, double* d_norm);
 
 /* Edge correction, Eqs. ModeCoupling and GammaMultipolesWithEC, Sec. 3.4: per (zt, b1, b2)

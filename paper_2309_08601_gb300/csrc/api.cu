@@ -643,7 +643,7 @@ mp3pcf_status mp3pcf_counts(mp3pcf_ctx* ctx, int64_t* h_n_centres, int64_t* h_n_
     MP3_CK(cudaMemcpyAsync(p, ctx->pairs.p, 16, cudaMemcpyDeviceToHost, ctx->st));
     MP3_CK(cudaStreamSynchronize(ctx->st));
     if (h_n_pairs) *h_n_pairs = (int64_t)p[0];
-    if (p[1]) return fail(ctx, MP3PCF_ETIMEOUT, "a bounded device wait in the moment kernel gave up");
+    if (p[1]) return fail(ctx, MP3PCF_ETIMEOUT, "a bounded device wait in the moment or contraction kernel gave up");
     return MP3PCF_OK;
 }
 
@@ -672,13 +672,30 @@ mp3pcf_status mp3pcf_contract_multipoles(mp3pcf_ctx* ctx, double* d_upsilon, dou
     if (!ctx || !d_upsilon || !d_norm) return fail(ctx, MP3PCF_EINVAL, "null argument");
     ctx->err.clear();
     const mp3pcf_config& c = ctx->cfg;
-    if (c.precision == MP3PCF_FP32_BF16X3 || c.precision == MP3PCF_FP32_TF32X3)
-        return fail(ctx, MP3PCF_EUNSUPPORTED, "tensor-core contraction not built");
     const int64_t nc = ctx->n_centres;
     if (nc == 0) return MP3PCF_OK;
     const int nz = c.n_z, nb = c.n_bins;
     const int z3 = nz * nz * nz;
     const int groups = z3 * groups_per_zt(c.n_max);
+    if (c.precision == MP3PCF_FP32_BF16X3 || c.precision == MP3PCF_FP32_TF32X3) {
+        // tensor-core form: plan the centre slices, size the partials, launch, reduce
+        const bool tf32 = c.precision == MP3PCF_FP32_TF32X3;
+        ContractArgs<float> a{ctx->G.as<cx<float>>(), ctx->W.as<cx<float>>(), ctx->pay.as<Pay<float>>(),
+                              ctx->zs.as<uint8_t>(), ctx->centre_idx.as<int>(), (int32_t)nc, nz, nb, c.n_max,
+                              0, nullptr};
+        int splits = 0;
+        unsigned long long* errw = ctx->pairs.as<unsigned long long>() + 1;
+        MP3_CK(launch_contract_tc(a, tf32, ctx->n_sm, errw, &splits, true, ctx->st));
+        MP3_CK(ctx->partial.ensure(sizeof(double) * 2 * (size_t)splits * groups * nb * nb));
+        a.splits = splits;
+        a.partial = ctx->partial.as<double>();
+        StageScope sc(ctx, ST_CONTRACT);
+        ctx->launches[ST_CONTRACT] += 2;
+        MP3_CK(launch_contract_tc(a, tf32, ctx->n_sm, errw, &splits, false, ctx->st));
+        MP3_CK(launch_contract_reduce(ctx->partial.as<double>(), splits, nz, nb, c.n_max, d_upsilon, d_norm,
+                                      ctx->st));
+        return MP3PCF_OK;
+    }
     int splits = (int)std::min<int64_t>(64, std::max<int64_t>(1, (int64_t)ctx->n_sm * 8 / groups));
     splits = (int)std::min<int64_t>(splits, std::max<int64_t>(1, nc / 256));
     MP3_CK(ctx->partial.ensure(sizeof(double) * 2 * (size_t)splits * groups * nb * nb));

@@ -115,6 +115,10 @@ struct ContractArgs {
 
 cudaError_t launch_contract_f32(const ContractArgs<float>& a, cudaStream_t st);
 cudaError_t launch_contract_f64(const ContractArgs<double>& a, cudaStream_t st);
+// tensor-core form (FP32 moments, BF16 or TF32 hi+lo split products); plan_only computes the
+// number of centre slices (*splits) without launching; err receives bit 2 if a bounded wait gave up
+cudaError_t launch_contract_tc(const ContractArgs<float>& a, bool tf32, int n_sm, unsigned long long* err,
+                               int* splits, bool plan_only, cudaStream_t st);
 cudaError_t launch_contract_reduce(const double* partial, int splits, int nz, int nb, int n_max,
                                    double* ups, double* norm, cudaStream_t st);
 
