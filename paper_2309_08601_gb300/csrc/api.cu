@@ -257,15 +257,17 @@ __global__ void k_centres(int64_t n, const int* __restrict__ perm, const int* __
 }
 
 template <typename T>
-__global__ void k_copy_rows(int64_t rows, int row_len, const int* __restrict__ crow,
+__global__ void k_copy_rows(int64_t rows, int sub, int len, int stride, const int* __restrict__ crow,
                             const cx<T>* __restrict__ src, cx<T>* __restrict__ dst)
 {
-    // src row r (sorted centre order) -> dst row crow[r]
-    const int64_t total = rows * row_len;
+    // src row r (sorted centre order; sub sub-rows of stride elements) -> dst row crow[r]
+    // (sub sub-rows of len elements)
+    const int64_t total = rows * sub * len;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = t / row_len, q = t % row_len;
-        dst[(int64_t)crow[r] * row_len + q] = src[t];
+        const int64_t q = t % len, rs = t / len;
+        const int64_t r = rs / sub, j = rs % sub;
+        dst[((int64_t)crow[r] * sub + j) * len + q] = src[rs * stride + q];
     }
 }
 
@@ -291,7 +293,7 @@ struct mp3pcf_ctx {
     DevBuf d_e2q, d_edges, d_nodes;
     DevBuf bb, key, count, fill, scan_sums, scan_total, perm, pos, pay, zs;
     DevBuf cflag, crank, oflag, orank, centre_idx, crow;
-    DevBuf G, W, pairs, partial, singular, m3partial;
+    DevBuf G, W, pairs, partial, singular, m3partial, ccoef;
     // tracing: per-stage event pairs and kernel-launch counts
     bool timing = false;
     int64_t launches[6] = {0, 0, 0, 0, 0, 0};
@@ -447,7 +449,7 @@ mp3pcf_status mp3pcf_destroy(mp3pcf_ctx* ctx)
                       &ctx->pos, &ctx->pay, &ctx->zs, &ctx->cflag,
                       &ctx->crank, &ctx->oflag, &ctx->orank, &ctx->centre_idx, &ctx->crow,
                       &ctx->G, &ctx->W, &ctx->pairs, &ctx->partial, &ctx->singular,
-                      &ctx->m3partial};
+                      &ctx->m3partial, &ctx->ccoef};
     for (DevBuf* b : bufs) b->release();
     for (auto& pr : ctx->ev) {
         cudaEventDestroy(pr.second.first);
@@ -587,9 +589,8 @@ static mp3pcf_status accumulate_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq,
     if (nc == 0) return MP3PCF_OK;
 
     // ---- stage (a)
-    const int MG = 2 * c.n_max + 3, MW = 2 * c.n_max + 1;
-    MP3_CK(ctx->G.ensure(sizeof(cx<T>) * (size_t)nc * nz * nb * MG));
-    MP3_CK(ctx->W.ensure(sizeof(cx<T>) * (size_t)nc * nz * nb * MW));
+    MP3_CK(ctx->G.ensure(sizeof(cx<T>) * (size_t)nc * nz * nb * g_stride(c.n_max)));
+    MP3_CK(ctx->W.ensure(sizeof(cx<T>) * (size_t)nc * nz * nb * w_stride(c.n_max)));
     MomentArgs<T> a;
     a.n_centres = nc;
     a.centre_idx = ctx->centre_idx.as<int>();
@@ -654,14 +655,15 @@ mp3pcf_status mp3pcf_copy_moments(mp3pcf_ctx* ctx, void* d_G, void* d_W)
     const int64_t nc = ctx->n_centres;
     if (nc == 0) return MP3PCF_OK;
     const mp3pcf_config& c = ctx->cfg;
-    const int rg = c.n_z * c.n_bins * (2 * c.n_max + 3), rw = c.n_z * c.n_bins * (2 * c.n_max + 1);
-    const unsigned gr = grid1d(nc * rg, ctx->n_sm);
+    const int sub = c.n_z * c.n_bins, lg = 2 * c.n_max + 3, lw = 2 * c.n_max + 1;
+    const int sg = g_stride(c.n_max), sw = w_stride(c.n_max);
+    const unsigned gr = grid1d(nc * sub * lg, ctx->n_sm);
     if (ctx->fp64) {
-        if (d_G) k_copy_rows<double><<<gr, 256, 0, ctx->st>>>(nc, rg, ctx->crow.as<int>(), ctx->G.as<cx<double>>(), (cx<double>*)d_G);
-        if (d_W) k_copy_rows<double><<<gr, 256, 0, ctx->st>>>(nc, rw, ctx->crow.as<int>(), ctx->W.as<cx<double>>(), (cx<double>*)d_W);
+        if (d_G) k_copy_rows<double><<<gr, 256, 0, ctx->st>>>(nc, sub, lg, sg, ctx->crow.as<int>(), ctx->G.as<cx<double>>(), (cx<double>*)d_G);
+        if (d_W) k_copy_rows<double><<<gr, 256, 0, ctx->st>>>(nc, sub, lw, sw, ctx->crow.as<int>(), ctx->W.as<cx<double>>(), (cx<double>*)d_W);
     } else {
-        if (d_G) k_copy_rows<float><<<gr, 256, 0, ctx->st>>>(nc, rg, ctx->crow.as<int>(), ctx->G.as<cx<float>>(), (cx<float>*)d_G);
-        if (d_W) k_copy_rows<float><<<gr, 256, 0, ctx->st>>>(nc, rw, ctx->crow.as<int>(), ctx->W.as<cx<float>>(), (cx<float>*)d_W);
+        if (d_G) k_copy_rows<float><<<gr, 256, 0, ctx->st>>>(nc, sub, lg, sg, ctx->crow.as<int>(), ctx->G.as<cx<float>>(), (cx<float>*)d_G);
+        if (d_W) k_copy_rows<float><<<gr, 256, 0, ctx->st>>>(nc, sub, lw, sw, ctx->crow.as<int>(), ctx->W.as<cx<float>>(), (cx<float>*)d_W);
     }
     MP3_CK(cudaGetLastError());
     return MP3PCF_OK;
@@ -685,13 +687,14 @@ mp3pcf_status mp3pcf_contract_multipoles(mp3pcf_ctx* ctx, double* d_upsilon, dou
                               0, nullptr};
         int splits = 0;
         unsigned long long* errw = ctx->pairs.as<unsigned long long>() + 1;
-        MP3_CK(launch_contract_tc(a, tf32, ctx->n_sm, errw, &splits, true, ctx->st));
+        MP3_CK(launch_contract_tc(a, tf32, ctx->n_sm, nullptr, errw, &splits, true, ctx->st));
         MP3_CK(ctx->partial.ensure(sizeof(double) * 2 * (size_t)splits * groups * nb * nb));
+        MP3_CK(ctx->ccoef.ensure(sizeof(float4) * (size_t)nc));
         a.splits = splits;
         a.partial = ctx->partial.as<double>();
         StageScope sc(ctx, ST_CONTRACT);
-        ctx->launches[ST_CONTRACT] += 2;
-        MP3_CK(launch_contract_tc(a, tf32, ctx->n_sm, errw, &splits, false, ctx->st));
+        ctx->launches[ST_CONTRACT] += 3;
+        MP3_CK(launch_contract_tc(a, tf32, ctx->n_sm, ctx->ccoef.as<float4>(), errw, &splits, false, ctx->st));
         MP3_CK(launch_contract_reduce(ctx->partial.as<double>(), splits, nz, nb, c.n_max, d_upsilon, d_norm,
                                       ctx->st));
         return MP3PCF_OK;

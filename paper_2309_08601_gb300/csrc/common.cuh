@@ -89,8 +89,8 @@ struct MomentArgs {
     GridDesc g;
     int32_t nz, nb, n_max;
     const long long* e2q;       // [nb + 1] exact squared edges in fixed-point units^2
-    cx<T>* G;                   // [n_centres][nz][nb][2 n_max + 3]
-    cx<T>* W;                   // [n_centres][nz][nb][2 n_max + 1]
+    cx<T>* G;                   // [n_centres][nz][nb][g_stride(n_max)]
+    cx<T>* W;                   // [n_centres][nz][nb][w_stride(n_max)]
     unsigned long long* pairs;  // [0] pair counter, [1] error flags (1: a bounded wait gave up)
 };
 
@@ -116,9 +116,10 @@ struct ContractArgs {
 cudaError_t launch_contract_f32(const ContractArgs<float>& a, cudaStream_t st);
 cudaError_t launch_contract_f64(const ContractArgs<double>& a, cudaStream_t st);
 // tensor-core form (FP32 moments, BF16 or TF32 hi+lo split products); plan_only computes the
-// number of centre slices (*splits) without launching; err receives bit 2 if a bounded wait gave up
-cudaError_t launch_contract_tc(const ContractArgs<float>& a, bool tf32, int n_sm, unsigned long long* err,
-                               int* splits, bool plan_only, cudaStream_t st);
+// number of centre slices (*splits) without launching; coef is scratch for n_centres float4;
+// err receives bit 2 if a bounded wait gave up
+cudaError_t launch_contract_tc(const ContractArgs<float>& a, bool tf32, int n_sm, float4* coef,
+                               unsigned long long* err, int* splits, bool plan_only, cudaStream_t st);
 cudaError_t launch_contract_reduce(const double* partial, int splits, int nz, int nb, int n_max,
                                    double* ups, double* norm, cudaStream_t st);
 
@@ -139,5 +140,11 @@ cudaError_t launch_to_map3(const PostArgs& p, const double* gcen, int n_ap, cons
                            cudaStream_t st);
 
 __host__ __device__ inline int groups_per_zt(int n_max) { return 4 * (n_max + 1) + 2 * n_max + 1; }
+
+// row strides (complex elements) of the moment arrays in device memory: the 2 n_max + 3 orders
+// of G and the 2 n_max + 1 orders of W, each padded by one element so that a row is a multiple
+// of 16 bytes (a requirement of tensor-memory-access copies); the pad is never written or used
+__host__ __device__ inline int g_stride(int n_max) { return 2 * n_max + 4; }
+__host__ __device__ inline int w_stride(int n_max) { return 2 * n_max + 2; }
 
 }  // namespace mp3

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kThreads) contract_kernel(const ContractArgs<T
         case 3: mx = n - 3; my = n - 1; yconj = true; break;      // G_{n-3} G_{n-1}^*
         default: mx = n; my = n; yconj = true; break;             // W_n W_n^*
     }
-    const int M = kind < 4 ? 2 * n_max + 3 : 2 * n_max + 1;
+    const int M = kind < 4 ? g_stride(n_max) : w_stride(n_max);
     const int off = kind < 4 ? n_max + 3 : 0;
     const cx<T>* src = kind < 4 ? a.G : a.W;
     const int nbb = nb * nb;

@@ -25,9 +25,11 @@
 // up sets bit 2 of the error word, stops the issue of further MMAs, waits (bounded) for those in
 // flight and frees the tensor memory. The per-slice FP32 sums are written as FP64 partials and
 // summed in a fixed order by contract_reduce_kernel, so results are deterministic.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -35,11 +37,13 @@ namespace mp3 {
 
 namespace tc {
 
-constexpr int kThreads = 256;  // 8 warps: two per TMEM lane quarter
+constexpr int kConvWarps = 8;                  // converter warps: two per TMEM lane quarter
+constexpr int kThreads = (kConvWarps + 2) * 32;  // + one TMA warp + one MMA warp
 constexpr int kM = 128;         // MMA rows (TMEM lanes)
 constexpr int kMaxGroups = 8;   // groups stacked in one tile
-constexpr int kTmemCols = 128;  // FP32 accumulator columns (N <= 128)
-constexpr int kFlush = 8;       // tiles per tensor-core accumulation chain
+constexpr int kTmemCols = 128;  // FP32 columns of one accumulator (N <= 128); two accumulators
+constexpr int kFlush = 32;      // tiles per tensor-core accumulation chain
+constexpr int kStages = 2;      // operand stages
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -86,7 +90,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, int parity, unsigned lon
 // the two split-precision forms: element size, centres per stage, K per MMA, operand format
 struct Bf16Split {
     static constexpr int ES = 2;
-    static constexpr int KT = 32;
+    static constexpr int KT = 16;
     static constexpr int KI = 16;
     static constexpr uint32_t FMT = 1;
     // hi and lo parts of two values packed as (first, second) in one 32-bit word each
@@ -110,7 +114,7 @@ struct Bf16Split {
 
 struct Tf32Split {
     static constexpr int ES = 4;
-    static constexpr int KT = 16;
+    static constexpr int KT = 8;
     static constexpr int KI = 8;
     static constexpr uint32_t FMT = 2;
     __device__ static uint32_t to_tf32(float x)
@@ -136,13 +140,25 @@ struct Tf32Split {
 
 struct TcArgs {
     ContractArgs<float> c;
-    int groups;   // nz^3 * groups_per_zt(n_max)
+    int groups;   // nz^3 * groups_per_zt(n_max): index space of the partial sums
     int gt;       // groups per tile
     int npad;     // MMA N: gt * 2 nb rounded up to 16
+    int bw;       // orders per TMA box (even, >= gt + 1)
+    int ta, tw;   // tiles per component of Upsilon (n_max + 1 orders) and of N (2 n_max + 1 orders)
     unsigned long long* err;
 };
 
-// one stage: A_hi, A_lo, B_hi, B_lo, each 128 rows x KT centres in the canonical no-swizzle
+// TMA boxes of one raw slot: X moments [KT][nb][bw] complex, Y moments (same), coefficients [KT]
+struct RawLayout {
+    int box_bytes, slot_bytes;
+    __host__ __device__ RawLayout(int kt, int nb, int bw)
+    {
+        box_bytes = kt * nb * bw * 8;
+        slot_bytes = ((2 * box_bytes + kt * 16) + 127) / 128 * 128;
+    }
+};
+
+// one operand stage: A_hi, A_lo, B_hi, B_lo, each 128 rows x KT centres in the canonical no-swizzle
 // K-major layout: element (r, k) at ((r/8)*(KT/T) + k/T)*128 B + (r%8)*16 B + (k%T)*ES
 template <class SP>
 struct Layout {
@@ -160,280 +176,442 @@ struct Layout {
     }
 };
 
-struct GroupInfo {
-    int z1, z2, z3, kind, mx, my;
-};
-
-// FP32 sums of the diagonal blocks in shared memory: dacc[t][i][j], i, j in [0, 2 nb)
-__device__ __forceinline__ int dacc_size(int ng, int nb) { return ng * 4 * nb * nb; }
+constexpr int kRaw = 3;  // raw slots: the TMA copies run two stages ahead of the conversion
 
 template <class SP>
-__global__ void __launch_bounds__(kThreads) contract_tc_kernel(const TcArgs a)
+static size_t smem_bytes(int kt, int nb, int bw, int gt)
+{
+    const RawLayout R(kt, nb, bw);
+    return (size_t)kRaw * R.slot_bytes + kStages * (size_t)Layout<SP>::STAGE_BYTES + (size_t)gt * nb * nb * sizeof(float2);
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// bounded wait that also gives up when another role has aborted
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, int parity, volatile int* abort, unsigned long long* err)
+{
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (*abort) return false;
+        if (clock64() - t0 > (1LL << 31)) {
+            if (err) atomicOr(err, 2ULL);
+            *abort = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// barriers among the converter warps only (named barrier 1); every converter thread reaches each
+// of them, also after an abort, so none can wait for a warp that left
+__device__ __forceinline__ void conv_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConvWarps * 32) : "memory"); }
+
+__device__ __forceinline__ bool conv_all(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.and.pred p, 1, %2, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kConvWarps * 32)
+        : "memory");
+    return r != 0;
+}
+
+// Grid: x = tiles of groups (a tile never spans two components or Z-triplets, so its orders are
+// consecutive), y = slices of the centre axis. Warp roles: warps 0..kConvWarps-1 convert raw
+// moments into split operands and flush the accumulators; warp kConvWarps issues the TMA copies;
+// warp kConvWarps+1 issues the MMAs. They synchronise only through mbarriers:
+//   rawfull[i]  (TMA bytes) -> converters     rawempty[i] (converter warps) -> TMA warp
+//   opfull[j]   (converter warps) -> MMA warp opempty[j]  (MMA commit) -> converters
+//   accfull[a]  (MMA commit) -> converters    accempty[a] (converter warps) -> MMA warp
+template <class SP>
+__global__ void __launch_bounds__(kThreads, 2) contract_tc_kernel(const __grid_constant__ CUtensorMap mapG,
+                                                               const __grid_constant__ CUtensorMap mapW,
+                                                               const __grid_constant__ CUtensorMap mapC,
+                                                               const TcArgs a)
 {
     using L = Layout<SP>;
     constexpr int KT = SP::KT;
     constexpr int PK = L::PK;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint32_t tmem_base;
-    __shared__ __align__(8) unsigned long long mbar[2];
-    __shared__ float4 coef_sm[KT];  // per centre of the stage: (w gamma_1, w gamma_2, w, zbin)
-    __shared__ GroupInfo gi[kMaxGroups];
+    __shared__ __align__(8) unsigned long long rawfull[kRaw], rawempty[kRaw], opfull[kStages], opempty[kStages],
+        accfull[2], accempty[2];
+    __shared__ volatile int abort_flag;
+    __shared__ int last_tma, last_mma;
 
     const ContractArgs<float>& A = a.c;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nb = A.nb, nz = A.nz, n_max = A.n_max;
-    const int nbb = nb * nb, nb2 = 2 * nb;
-    const int g0 = blockIdx.x * a.gt;
-    const int ng = min(a.gt, a.groups - g0);
+    const int nbb = nb * nb, nb2 = 2 * nb, bw = a.bw;
+
+    // ---- the tile: Z-triplet, component, first order, number of groups
+    const int per_tile_zt = 4 * a.ta + a.tw;
+    const int zt = blockIdx.x / per_tile_zt, r = blockIdx.x % per_tile_zt;
+    int kind, n0, ng;
+    if (r < 4 * a.ta) {
+        kind = r / a.ta;
+        n0 = (r % a.ta) * a.gt;
+        ng = min(a.gt, n_max + 1 - n0);
+    } else {
+        kind = 4;
+        n0 = (r - 4 * a.ta) * a.gt;
+        ng = min(a.gt, 2 * n_max + 1 - n0);
+    }
+    const int z1 = zt / (nz * nz), z2 = (zt / nz) % nz, z3 = zt % nz;
+    const int gbase = zt * groups_per_zt(n_max) + (kind < 4 ? kind * (n_max + 1) : 4 * (n_max + 1)) + n0;
+    // orders of group t: X m = ax + sx t, Y m = ay + sy t (as in the SIMT form)
+    int ax, sx, ay, sy;
+    switch (kind) {
+        case 0: ax = n0 - 3; sx = 1; ay = -n0 - 3; sy = -1; break;   // G_{n-3} G_{-n-3}
+        case 1: ax = n0 - 1; sx = 1; ay = -n0 - 1; sy = -1; break;   // G_{n-1} G_{-n-1}
+        case 2: ax = -n0 - 1; sx = -1; ay = -n0 - 3; sy = -1; break; // G_{-n-1}^* G_{-n-3}
+        case 3: ax = n0 - 3; sx = 1; ay = n0 - 1; sy = 1; break;     // G_{n-3} G_{n-1}^*
+        default: ax = n0; sx = 1; ay = n0; sy = 1; break;            // W_n W_n^*
+    }
+    const int off = kind < 4 ? n_max + 3 : 0;
+    // first element of each box: the lowest order index, rounded down to an even element so the
+    // box starts on a 16-byte boundary
+    const int ix0 = ((sx > 0 ? ax : ax - (ng - 1)) + off) & ~1;
+    const int iy0 = ((sy > 0 ? ay : ay - (ng - 1)) + off) & ~1;
+    const CUtensorMap* mapM = kind < 4 ? &mapG : &mapW;
+
     const int sl = blockIdx.y, slices = gridDim.y;
     const int per = (A.n_centres + slices - 1) / slices;
     const int c0 = min(A.n_centres, sl * per), c1 = min(A.n_centres, c0 + per);
     const int ntiles = (c1 - c0 + KT - 1) / KT;
-    const int MG = 2 * n_max + 3, MW = 2 * n_max + 1;
-    float* dacc = reinterpret_cast<float*>(smem + 2 * L::STAGE_BYTES);
+    const int nchains = (ntiles + kFlush - 1) / kFlush;
 
-    if (tid < ng) {
-        const int per_zt = groups_per_zt(n_max);
-        const int g = g0 + tid;
-        const int zt = g / per_zt, loc = g % per_zt;
-        GroupInfo q;
-        q.z1 = zt / (nz * nz);
-        q.z2 = (zt / nz) % nz;
-        q.z3 = zt % nz;
-        int n;
-        if (loc < 4 * (n_max + 1)) {
-            q.kind = loc / (n_max + 1);
-            n = loc % (n_max + 1);
-        } else {
-            q.kind = 4;
-            n = loc - 4 * (n_max + 1);
-        }
-        // orders of the first (X) and second (Y) moment, as in the SIMT form
-        switch (q.kind) {
-            case 0: q.mx = n - 3; q.my = -n - 3; break;   // G_{n-3} G_{-n-3}
-            case 1: q.mx = n - 1; q.my = -n - 1; break;   // G_{n-1} G_{-n-1}
-            case 2: q.mx = -n - 1; q.my = -n - 3; break;  // G_{-n-1}^* G_{-n-3}
-            case 3: q.mx = n - 3; q.my = n - 1; break;    // G_{n-3} G_{n-1}^*
-            default: q.mx = n; q.my = n; break;           // W_n W_n^*
-        }
-        gi[tid] = q;
-    }
+    const RawLayout R(KT, nb, bw);
+    unsigned char* raw = smem;
+    unsigned char* ops = smem + kRaw * R.slot_bytes;
+    float2* dacc = reinterpret_cast<float2*>(ops + kStages * L::STAGE_BYTES);  // [ng][nb][nb] (re, im)
+
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(kTmemCols));
+                     "r"(2 * kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        mbar_init(smem_u32(&mbar[0]), 1);
-        mbar_init(smem_u32(&mbar[1]), 1);
+        for (int i = 0; i < kRaw; ++i) {
+            mbar_init(smem_u32(&rawfull[i]), 1);
+            mbar_init(smem_u32(&rawempty[i]), kConvWarps);
+        }
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(smem_u32(&opfull[i]), kConvWarps);
+            mbar_init(smem_u32(&opempty[i]), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&accfull[i]), 1);
+            mbar_init(smem_u32(&accempty[i]), kConvWarps);
+        }
+        abort_flag = 0;
+        last_tma = 0;
+        last_mma = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // zero both stages (rows outside the stacked groups stay zero) and the block sums
-    const int zero16 = (2 * L::STAGE_BYTES + dacc_size(ng, nb) * 4 + 15) / 16;
-    for (int i = tid; i < zero16; i += kThreads) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
+    // zero the operand stages (rows outside the stacked groups stay zero) and the block sums
+    {
+        uint4* z = reinterpret_cast<uint4*>(ops);
+        const int n16 = (kStages * L::STAGE_BYTES + ng * nbb * 8 + 15) / 16;
+        for (int i = tid; i < n16; i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = (1u << 4) | (SP::FMT << 7) | (SP::FMT << 10) | ((uint32_t)(a.npad >> 3) << 17) |
-                           ((uint32_t)(kM >> 4) << 24);
-    const int TB = ng * nb;
-    const int items = L::KW * TB;
 
-    // TMEM lane quarter and column half this warp reads; the accumulator row it holds
-    const int quarter = warp & 3, half = warp >> 2;
-    const int row = quarter * 32 + lane;
-    const int rt = row / nb2, ri = row % nb2;  // group and row within the group's block
-    const int ncol = a.npad / 2, colb = half * ncol;
-
-    // adds the accumulator (the sums of the tiles since the last flush) to dacc, after the MMAs
-    // of tile t completed; false if the bounded wait gave up
-    auto flush = [&](int t) -> bool {
-        const bool done = mbar_wait(smem_u32(&mbar[t & 1]), (t >> 1) & 1, a.err);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (__all_sync(0xffffffffu, done)) {
-            for (int col = colb; col < colb + ncol; col += 8) {
-                uint32_t r[8];
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                               "=r"(r[6]), "=r"(r[7])
-                             : "r"(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (rt < ng) {
+    if (warp == kConvWarps) {
+        // ================= TMA warp: copies of tile s into raw slot s % kRaw
+        if (lane == 0) {
+            const uint32_t tx_bytes = 2 * R.box_bytes + KT * 16;
+            for (int s = 0; s < ntiles; ++s) {
+                const int slot = s % kRaw;
+                if (s >= kRaw && !wait_or_abort(smem_u32(&rawempty[slot]), ((s / kRaw) - 1) & 1, &abort_flag, a.err))
+                    break;
+                const uint32_t dst = smem_u32(raw + slot * R.slot_bytes);
+                const uint32_t bar = smem_u32(&rawfull[slot]);
+                const int cb = c0 + s * KT;
+                mbar_expect_tx(bar, tx_bytes);
+                tma_load_3d(dst, mapM, 2 * ix0, z2 * nb, cb, bar);
+                tma_load_3d(dst + R.box_bytes, mapM, 2 * iy0, z3 * nb, cb, bar);
+                tma_load_2d(dst + 2 * R.box_bytes, &mapC, 0, cb, bar);
+                last_tma = s + 1;
+            }
+        }
+    } else if (warp == kConvWarps + 1) {
+        // ================= MMA warp: three split products per K-step into accumulator chain % 2
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (SP::FMT << 7) | (SP::FMT << 10) |
+                                   ((uint32_t)(a.npad >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+            for (int s = 0; s < ntiles; ++s) {
+                const int st = s % kStages, c = s / kFlush;
+                const bool first = s % kFlush == 0;
+                if (first && c >= 2 &&
+                    !wait_or_abort(smem_u32(&accempty[c & 1]), ((c >> 1) - 1) & 1, &abort_flag, a.err))
+                    break;
+                if (!wait_or_abort(smem_u32(&opfull[st]), (s / kStages) & 1, &abort_flag, a.err)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)((c & 1) * kTmemCols);
+                const uint32_t s0 = smem_u32(ops + st * L::STAGE_BYTES);
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int cj = col + j - rt * nb2;
-                        if (cj >= 0 && cj < nb2) dacc[(rt * nb2 + ri) * nb2 + cj] += __uint_as_float(r[j]);
-                    }
+                for (int kk = 0; kk < KT / SP::KI; ++kk) {
+                    const uint32_t ko = kk * 256;  // two core matrices along K per MMA
+                    const uint64_t ah = smem_desc(s0 + 0 * L::OP_BYTES + ko, 128, L::SBO);
+                    const uint64_t al = smem_desc(s0 + 1 * L::OP_BYTES + ko, 128, L::SBO);
+                    const uint64_t bh = smem_desc(s0 + 2 * L::OP_BYTES + ko, 128, L::SBO);
+                    const uint64_t bl = smem_desc(s0 + 3 * L::OP_BYTES + ko, 128, L::SBO);
+                    SP::mma(d, ah, bh, idesc, (first && kk == 0) ? 0u : 1u);
+                    SP::mma(d, ah, bl, idesc, 1u);
+                    SP::mma(d, al, bh, idesc, 1u);
                 }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&opempty[st]))
+                             : "memory");
+                if (s % kFlush == kFlush - 1 || s == ntiles - 1)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(&accfull[c & 1]))
+                                 : "memory");
+                last_mma = s + 1;
             }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        const bool all = __syncthreads_and(done);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        return all;
-    };
-
-    int issued = 0;
-    bool ok = true;
-    for (int tile = 0; tile < ntiles; ++tile) {
-        const int st = tile & 1;
-        unsigned char* sbase = smem + st * L::STAGE_BYTES;
-        // the stage is free once the MMAs issued on it two tiles ago have completed
-        bool good = true;
-        if (tid == 0 && tile >= 2) good = mbar_wait(smem_u32(&mbar[st]), ((tile - 2) >> 1) & 1, a.err);
-        const int cb = c0 + tile * KT;
-        if (tid < KT) {
-            const int c = cb + tid;
-            float4 cf = make_float4(0.f, 0.f, 0.f, -1.f);
-            if (c < c1) {
-                const int d = A.centre_idx[c];
-                const Pay<float> pv = A.pay[d];
-                cf = make_float4(pv.a, pv.b, pv.w, (float)(A.zs ? (int)A.zs[d] : 0));
-            }
-            coef_sm[tid] = cf;
-        }
-        if (!__syncthreads_and(good)) {
-            ok = false;
-            break;
-        }
-
-        // item = (word column kw, group t, bin b); 4 consecutive lanes fill one 16-byte core
-        // row, 8 lane quads fill 8 different rows: conflict-free 32-bit stores
-        for (int it = tid; it < items; it += kThreads) {
+    } else {
+        // ================= converter warps
+        // this thread's conversion items, the same in every stage: item = (word column kw, group
+        // t, bin b); 4 consecutive lanes fill one 16-byte core row, 8 lane quads fill 8 rows
+        constexpr int kItems = 2;  // KW * ng * nb <= 8 * 64 = 512 = 2 * kConvWarps * 32
+        const int TB = ng * nb;
+        const int items = L::KW * TB;
+        uint32_t i_ore[kItems], i_oim[kItems];
+        int i_xo[kItems], i_yo[kItems], i_k[kItems];
+#pragma unroll
+        for (int q = 0; q < kItems; ++q) {
+            const int it = tid + q * kConvWarps * 32;
             const int kw_lo = it & 3, rest = it >> 2;
             const int tb = rest % TB, kw = (rest / TB) * 4 + kw_lo;
             const int t = tb / nb, b = tb % nb;
-            const GroupInfo q = gi[t];
-            const bool isW = q.kind == 4;
-            const cx<float>* src = isW ? A.W : A.G;
-            const int M = isW ? MW : MG, off = isW ? 0 : n_max + 3;
-            float xr[PK], xi[PK], yr[PK], yi[PK];
+            const int ox = ax + sx * t + off - ix0, oy = ay + sy * t + off - iy0;  // order offset in the box
+            const int rre = t * nb2 + b;
+            i_ore[q] = L::word_off(rre, kw);
+            i_oim[q] = L::word_off(rre + nb, kw);
+            i_k[q] = it < items ? kw * PK : 1 << 20;  // first centre of the word; out of range: no item
+            i_xo[q] = (kw * PK * nb + b) * bw + ox;   // complex index in the X box
+            i_yo[q] = (kw * PK * nb + b) * bw + oy;
+        }
+        // L = coef X with coef = -(w gamma), -(w gamma)^* or w; conjugations as signs
+        const float ca = kind == 4 ? 0.f : -1.f, cw = kind == 4 ? 1.f : 0.f;
+        const float cb_ = kind == 4 ? 0.f : (kind == 1 ? 1.f : -1.f);
+        const float xs = kind == 2 ? -1.f : 1.f, ys = kind >= 3 ? -1.f : 1.f;
+        const float fz1 = (float)z1;
+        // TMEM lane quarter and column half this warp reads; the accumulator row it holds
+        const int quarter = warp & 3, half = warp >> 2;
+        const int row = quarter * 32 + lane;
+        const int rt = row / nb2, ri = row % nb2;
+        const bool re_row = ri < nb;
+        const int b1 = re_row ? ri : ri - nb;
+        const int ncol = a.npad / 2, colb = half * ncol;
+
+        // adds chain c's accumulator to dacc (Re rows, then Im rows: one writer per element and
+        // phase) and hands the accumulator back to the MMA warp
+        auto flush = [&](int c, bool go) -> bool {
+            if (go) go = wait_or_abort(smem_u32(&accfull[c & 1]), (c >> 1) & 1, &abort_flag, a.err);
+            if (!conv_all(go)) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((c & 1) * kTmemCols);
+            for (int phase = 0; phase < 2; ++phase) {
+                const bool mine = rt < ng && re_row == (phase == 0);
+                float2* D = dacc + (rt * nb + b1) * nb;
+                for (int col = colb; col < colb + ncol; col += 8) {
+                    uint32_t v[8];
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                                   "=r"(v[6]), "=r"(v[7])
+                                 : "r"(base + (uint32_t)col));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (mine) {
 #pragma unroll
-            for (int p = 0; p < PK; ++p) {
-                const int k = kw * PK + p, c = cb + k;
-                const float4 cf = coef_sm[k];
-                cx<float> X{0.f, 0.f}, Y{0.f, 0.f};
-                if (c < c1 && (int)cf.w == q.z1) {
-                    const float2 xv = __ldg(reinterpret_cast<const float2*>(
-                        src + (((size_t)c * nz + q.z2) * nb + b) * M + q.mx + off));
-                    const float2 yv = __ldg(reinterpret_cast<const float2*>(
-                        src + (((size_t)c * nz + q.z3) * nb + b) * M + q.my + off));
-                    X = {xv.x, xv.y};
-                    Y = {yv.x, yv.y};
-                    if (q.kind == 2) X = cconj(X);
-                    if (q.kind >= 3) Y = cconj(Y);
-                    cx<float> co;
-                    if (isW)
-                        co = {cf.z, 0.f};
-                    else if (q.kind == 1)
-                        co = {-cf.x, cf.y};  // -(w gamma)^*
-                    else
-                        co = {-cf.x, -cf.y};  // -(w gamma)
-                    X = cmul(co, X);
+                        for (int q = 0; q < 8; ++q) {
+                            const int j = col + q - rt * nb2;
+                            if (j >= 0 && j < nb2) {
+                                const float x = __uint_as_float(v[q]);
+                                const bool re_col = j < nb;
+                                float2* e = D + (re_col ? j : j - nb);
+                                if (re_row) {
+                                    if (re_col) e->x += x;  // Re L Re R
+                                    else e->y += x;         // Re L Im R
+                                } else {
+                                    if (re_col) e->y += x;  // Im L Re R
+                                    else e->x -= x;         // - Im L Im R
+                                }
+                            }
+                        }
+                    }
                 }
-                xr[p] = X.x;
-                xi[p] = X.y;
-                yr[p] = Y.x;
-                yi[p] = Y.y;
+                conv_sync();
             }
-            uint32_t h[4], l[4];
-            if constexpr (PK == 2) {
-                SP::split2(xr[0], xr[PK - 1], h[0], l[0]);
-                SP::split2(xi[0], xi[PK - 1], h[1], l[1]);
-                SP::split2(yr[0], yr[PK - 1], h[2], l[2]);
-                SP::split2(yi[0], yi[PK - 1], h[3], l[3]);
-            } else {
-                SP::split1(xr[0], h[0], l[0]);
-                SP::split1(xi[0], h[1], l[1]);
-                SP::split1(yr[0], h[2], l[2]);
-                SP::split1(yi[0], h[3], l[3]);
-            }
-            const int rre = t * nb2 + b, rim = rre + nb;
-            const uint32_t ore = L::word_off(rre, kw), oim = L::word_off(rim, kw);
-            *reinterpret_cast<uint32_t*>(sbase + 0 * L::OP_BYTES + ore) = h[0];
-            *reinterpret_cast<uint32_t*>(sbase + 1 * L::OP_BYTES + ore) = l[0];
-            *reinterpret_cast<uint32_t*>(sbase + 0 * L::OP_BYTES + oim) = h[1];
-            *reinterpret_cast<uint32_t*>(sbase + 1 * L::OP_BYTES + oim) = l[1];
-            *reinterpret_cast<uint32_t*>(sbase + 2 * L::OP_BYTES + ore) = h[2];
-            *reinterpret_cast<uint32_t*>(sbase + 3 * L::OP_BYTES + ore) = l[2];
-            *reinterpret_cast<uint32_t*>(sbase + 2 * L::OP_BYTES + oim) = h[3];
-            *reinterpret_cast<uint32_t*>(sbase + 3 * L::OP_BYTES + oim) = l[3];
-        }
-        // make the generic-proxy stores visible to the tensor core
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // every kFlush tiles the accumulator is added to the FP32 block sums and restarted, so
-        // no tensor-core accumulation chain is longer than 3 kFlush (KT / KI) MMAs
-        bool fresh = tile == 0;
-        if (tile > 0 && tile % kFlush == 0) {
-            if (!flush(tile - 1)) {
-                ok = false;
-                break;
-            }
-            fresh = true;
-        }
-        if (tid == 0) {
-            const uint32_t s0 = smem_u32(sbase);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&accempty[c & 1]));
+            return true;
+        };
+
+        int flushed = 0;
+        bool good = true;
+        for (int s = 0; s < ntiles; ++s) {
+            const int slot = s % kRaw, st = s % kStages;
+            if (good) good = wait_or_abort(smem_u32(&rawfull[slot]), (s / kRaw) & 1, &abort_flag, a.err);
+            if (good && s >= kStages)
+                good = wait_or_abort(smem_u32(&opempty[st]), ((s / kStages) - 1) & 1, &abort_flag, a.err);
+            if (good) {
+                // ---- convert: L = coef X (conj), R = Y (conj), split hi/lo into the operand layout
+                const float2* rx = reinterpret_cast<const float2*>(raw + slot * R.slot_bytes);
+                const float2* ry = reinterpret_cast<const float2*>(raw + slot * R.slot_bytes + R.box_bytes);
+                const float4* rc = reinterpret_cast<const float4*>(raw + slot * R.slot_bytes + 2 * R.box_bytes);
+                unsigned char* sbase = ops + st * L::STAGE_BYTES;
+                const int kend = c1 - (c0 + s * KT);  // centres of this stage inside the slice
 #pragma unroll
-            for (int kk = 0; kk < KT / SP::KI; ++kk) {
-                const uint32_t ko = kk * 256;  // two core matrices along K per MMA
-                const uint64_t ah = smem_desc(s0 + 0 * L::OP_BYTES + ko, 128, L::SBO);
-                const uint64_t al = smem_desc(s0 + 1 * L::OP_BYTES + ko, 128, L::SBO);
-                const uint64_t bh = smem_desc(s0 + 2 * L::OP_BYTES + ko, 128, L::SBO);
-                const uint64_t bl = smem_desc(s0 + 3 * L::OP_BYTES + ko, 128, L::SBO);
-                SP::mma(tmem, ah, bh, idesc, (fresh && kk == 0) ? 0u : 1u);
-                SP::mma(tmem, ah, bl, idesc, 1u);
-                SP::mma(tmem, al, bh, idesc, 1u);
+                for (int q = 0; q < kItems; ++q) {
+                    if (i_k[q] >= KT) continue;
+                    float xr[PK], xi[PK], yr[PK], yi[PK];
+#pragma unroll
+                    for (int p = 0; p < PK; ++p) {
+                        const int k = i_k[q] + p;
+                        const float4 cf = rc[k];
+                        float2 X = rx[i_xo[q] + p * nb * bw], Y = ry[i_yo[q] + p * nb * bw];
+                        const bool use = k < kend && cf.w == fz1;
+                        const float cr = ca * cf.x + cw * cf.z, ci = cb_ * cf.y;
+                        X.y *= xs;
+                        const float lx = cr * X.x - ci * X.y, ly = cr * X.y + ci * X.x;
+                        xr[p] = use ? lx : 0.f;
+                        xi[p] = use ? ly : 0.f;
+                        yr[p] = use ? Y.x : 0.f;
+                        yi[p] = use ? ys * Y.y : 0.f;
+                    }
+                    uint32_t h[4], l[4];
+                    if constexpr (PK == 2) {
+                        SP::split2(xr[0], xr[PK - 1], h[0], l[0]);
+                        SP::split2(xi[0], xi[PK - 1], h[1], l[1]);
+                        SP::split2(yr[0], yr[PK - 1], h[2], l[2]);
+                        SP::split2(yi[0], yi[PK - 1], h[3], l[3]);
+                    } else {
+                        SP::split1(xr[0], h[0], l[0]);
+                        SP::split1(xi[0], h[1], l[1]);
+                        SP::split1(yr[0], h[2], l[2]);
+                        SP::split1(yi[0], h[3], l[3]);
+                    }
+                    *reinterpret_cast<uint32_t*>(sbase + 0 * L::OP_BYTES + i_ore[q]) = h[0];
+                    *reinterpret_cast<uint32_t*>(sbase + 1 * L::OP_BYTES + i_ore[q]) = l[0];
+                    *reinterpret_cast<uint32_t*>(sbase + 0 * L::OP_BYTES + i_oim[q]) = h[1];
+                    *reinterpret_cast<uint32_t*>(sbase + 1 * L::OP_BYTES + i_oim[q]) = l[1];
+                    *reinterpret_cast<uint32_t*>(sbase + 2 * L::OP_BYTES + i_ore[q]) = h[2];
+                    *reinterpret_cast<uint32_t*>(sbase + 3 * L::OP_BYTES + i_ore[q]) = l[2];
+                    *reinterpret_cast<uint32_t*>(sbase + 2 * L::OP_BYTES + i_oim[q]) = h[3];
+                    *reinterpret_cast<uint32_t*>(sbase + 3 * L::OP_BYTES + i_oim[q]) = l[3];
+                }
+                // make the generic-proxy stores visible to the tensor core; hand over the stage
+                // and give the raw slot back to the TMA warp
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(smem_u32(&opfull[st]));
+                    mbar_arrive(smem_u32(&rawempty[slot]));
+                }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&mbar[st]))
-                         : "memory");
+            // flush the previous chain once the next one is two tiles in (its MMAs are done by
+            // then); all converter warps take part, so an abort ends the loop for all of them
+            if (s % kFlush == 1 && s > kFlush) {
+                good = flush(flushed, good);
+                if (!good) break;
+                ++flushed;
+            }
         }
-        issued = tile + 1;
+        // the remaining chains
+        good = conv_all(good);
+        while (good && flushed < nchains) {
+            good = flush(flushed, true);
+            ++flushed;
+        }
     }
 
-    if (ok && ntiles > 0) {
-        ok = flush(ntiles - 1);
-    } else if (issued > 0) {
-        // a wait gave up: wait (bounded) for this thread's last commit, which tracks all MMAs
-        if (tid == 0) mbar_wait(smem_u32(&mbar[(issued - 1) & 1]), ((issued - 1) >> 1) & 1, a.err);
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    const bool ok = !abort_flag;
+    if (!ok) {
+        // a wait gave up: wait (bounded) for the copies still in flight and for the MMA warp's
+        // last commit, which tracks all its MMAs, before the shared and tensor memory are freed
+        if (warp == kConvWarps && lane == 0)
+            for (int i = 0; i < kRaw; ++i) {
+                const int s = last_tma - 1 - i;  // the last copy issued into each slot
+                if (s >= 0) mbar_wait(smem_u32(&rawfull[s % kRaw]), (s / kRaw) & 1, a.err);
+            }
+        if (warp == kConvWarps + 1 && lane == 0 && last_mma > 0)
+            mbar_wait(smem_u32(&opempty[(last_mma - 1) % kStages]), ((last_mma - 1) / kStages) & 1, a.err);
         __syncthreads();
     }
-    // diagonal blocks: (Re L Re R - Im L Im R, Re L Im R + Im L Re R), in FP64
+    // the complex block sums, in FP64
     for (int it = tid; it < ng * nbb; it += kThreads) {
-        const int t = it / nbb, o = it % nbb, b1 = o / nb, b2 = o % nb;
-        double re = 0.0, im = 0.0;
-        if (ok) {
-            const float* D = dacc + t * nb2 * nb2;
-            re = (double)D[b1 * nb2 + b2] - (double)D[(nb + b1) * nb2 + nb + b2];
-            im = (double)D[b1 * nb2 + nb + b2] + (double)D[(nb + b1) * nb2 + b2];
-        }
-        double* dst = A.partial + 2 * (((size_t)sl * a.groups + (g0 + t)) * nbb + o);
-        dst[0] = re;
-        dst[1] = im;
+        const float2 v = ok ? dacc[it] : make_float2(0.f, 0.f);
+        const int t = it / nbb, o = it % nbb;
+        double* dst = A.partial + 2 * (((size_t)sl * a.groups + (gbase + t)) * nbb + o);
+        dst[0] = (double)v.x;
+        dst[1] = (double)v.y;
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTmemCols));
     }
 }
 
-template <class SP>
-static size_t smem_bytes(int gt, int nb)
+// per-centre coefficients in centre order for the coefficient boxes: (w gamma_1, w gamma_2, w, zbin)
+__global__ void centre_coef_kernel(int n, const int32_t* __restrict__ centre_idx, const Pay<float>* __restrict__ pay,
+                                   const uint8_t* __restrict__ zs, float4* __restrict__ out)
 {
-    return 2 * (size_t)Layout<SP>::STAGE_BYTES + (size_t)gt * 4 * nb * nb * sizeof(float);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const int d = centre_idx[c];
+        const Pay<float> p = pay[d];
+        out[c] = make_float4(p.a, p.b, p.w, (float)(zs ? (int)zs[d] : 0));
+    }
 }
 
-// slices of the centre axis: fill the resident CTA slots in whole waves, at least 4 stages
+// slices of the centre axis: fill the resident CTA slots in whole waves, at least 8 stages
 // of centres per slice, at most 64 slices
 static int pick_slices(int tiles, int slots, int64_t n_centres, int kt)
 {
-    const int64_t smax = std::max<int64_t>(1, std::min<int64_t>(64, n_centres / (4 * kt)));
+    const int64_t smax = std::max<int64_t>(1, std::min<int64_t>(64, n_centres / (8 * kt)));
     int best = 1;
     double best_score = -1.0;
     for (int s = 1; s <= smax; ++s) {
@@ -449,29 +627,83 @@ static int pick_slices(int tiles, int slots, int64_t n_centres, int kt)
     return best;
 }
 
-template <class SP>
-static cudaError_t launch_tc(TcArgs a, int n_sm, int* splits_out, bool plan_only, cudaStream_t st)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
 {
-    const size_t smem = smem_bytes<SP>(a.gt, a.c.nb);
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// FP32 tensor of rank 2 or 3 (dims innermost first, strides in bytes of dims 1..), boxes as given
+static bool encode(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
+                   const uint32_t* box)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<void*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <class SP>
+static cudaError_t launch_tc(TcArgs a, float4* coef, int n_sm, int* splits_out, bool plan_only, cudaStream_t st)
+{
+    const ContractArgs<float>& c = a.c;
+    const size_t smem = smem_bytes<SP>(SP::KT, c.nb, a.bw, a.gt);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, contract_tc_kernel<SP>, kThreads, smem);
     if (e != cudaSuccess) return e;
-    per_sm = std::max(1, std::min(per_sm, 512 / kTmemCols));
-    const int tiles = (a.groups + a.gt - 1) / a.gt;
-    const int slices = pick_slices(tiles, per_sm * n_sm, a.c.n_centres, SP::KT);
+    per_sm = std::max(1, std::min(per_sm, 512 / (2 * kTmemCols)));
+    const int tiles = c.nz * c.nz * c.nz * (4 * a.ta + a.tw);
+    const int slices = pick_slices(tiles, per_sm * n_sm, c.n_centres, SP::KT);
     *splits_out = slices;
     if (plan_only) return cudaSuccess;
-    if (slices != a.c.splits) return cudaErrorInvalidValue;  // partial buffer sized for another plan
-    contract_tc_kernel<SP><<<dim3(tiles, slices), kThreads, smem, st>>>(a);
+    if (slices != c.splits) return cudaErrorInvalidValue;  // partial buffer sized for another plan
+
+    // tensor maps: moments [n_centres][nz * nb][stride] complex as FP32 (innermost first)
+    const uint64_t rows = (uint64_t)c.nz * c.nb, nc = (uint64_t)c.n_centres;
+    const uint64_t sg = g_stride(c.n_max), sw = w_stride(c.n_max);
+    const uint32_t box[3] = {(uint32_t)(2 * a.bw), (uint32_t)c.nb, (uint32_t)SP::KT};
+    CUtensorMap mg, mw, mc;
+    {
+        const uint64_t d[3] = {2 * sg, rows, nc}, s[2] = {sg * 8, rows * sg * 8};
+        if (!encode(&mg, c.G, 3, d, s, box)) return cudaErrorInvalidValue;
+    }
+    {
+        const uint64_t d[3] = {2 * sw, rows, nc}, s[2] = {sw * 8, rows * sw * 8};
+        if (!encode(&mw, c.W, 3, d, s, box)) return cudaErrorInvalidValue;
+    }
+    {
+        const uint64_t d[2] = {4, nc}, s[1] = {16};
+        const uint32_t b2[2] = {4, (uint32_t)SP::KT};
+        if (!encode(&mc, coef, 2, d, s, b2)) return cudaErrorInvalidValue;
+    }
+    centre_coef_kernel<<<(unsigned)std::min<int64_t>((nc + 255) / 256, 4 * n_sm), 256, 0, st>>>(
+        c.n_centres, c.centre_idx, c.pay, c.zs, coef);
+    contract_tc_kernel<SP><<<dim3(tiles, slices), kThreads, smem, st>>>(mg, mw, mc, a);
     return cudaGetLastError();
 }
 
 }  // namespace tc
 
-cudaError_t launch_contract_tc(const ContractArgs<float>& c, bool tf32, int n_sm, unsigned long long* err,
-                               int* splits, bool plan_only, cudaStream_t st)
+cudaError_t launch_contract_tc(const ContractArgs<float>& c, bool tf32, int n_sm, float4* coef,
+                               unsigned long long* err, int* splits, bool plan_only, cudaStream_t st)
 {
     tc::TcArgs a;
     a.c = c;
@@ -479,9 +711,12 @@ cudaError_t launch_contract_tc(const ContractArgs<float>& c, bool tf32, int n_sm
     a.gt = std::min(tc::kMaxGroups, tc::kM / (2 * c.nb));
     if (a.gt < 1) return cudaErrorInvalidValue;
     a.npad = ((a.gt * 2 * c.nb + 15) / 16) * 16;
+    a.bw = (a.gt + 2) & ~1;
+    a.ta = (c.n_max + 1 + a.gt - 1) / a.gt;
+    a.tw = (2 * c.n_max + 1 + a.gt - 1) / a.gt;
     a.err = err;
-    return tf32 ? tc::launch_tc<tc::Tf32Split>(a, n_sm, splits, plan_only, st)
-                : tc::launch_tc<tc::Bf16Split>(a, n_sm, splits, plan_only, st);
+    return tf32 ? tc::launch_tc<tc::Tf32Split>(a, coef, n_sm, splits, plan_only, st)
+                : tc::launch_tc<tc::Bf16Split>(a, coef, n_sm, splits, plan_only, st);
 }
 
 }  // namespace mp3

@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(MomPlan<T, NMAX>::NT, MomPlan<T, NMAX>::MINB) 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int nb = A.nb, nz = A.nz, n_max = A.n_max;
-    const int MG = 2 * n_max + 3, MW = 2 * n_max + 1;
+    const int MG = g_stride(n_max), MW = w_stride(n_max);  // padded row strides
     const float S = (float)A.g.side, iS = 1.0f / S;
     // the last order slot of this warp may fall outside the order range
     const bool lastW = warp + (NWM - 1) * P <= 2 * NMAX;
