@@ -257,17 +257,21 @@ __global__ void k_centres(int64_t n, const int* __restrict__ perm, const int* __
 }
 
 template <typename T>
-__global__ void k_copy_rows(int64_t rows, int sub, int len, int stride, const int* __restrict__ crow,
+__global__ void k_copy_rows(int64_t nc, int nz, int nb, int len, const int* __restrict__ crow,
                             const cx<T>* __restrict__ src, cx<T>* __restrict__ dst)
 {
-    // src row r (sorted centre order; sub sub-rows of stride elements) -> dst row crow[r]
-    // (sub sub-rows of len elements)
-    const int64_t total = rows * sub * len;
+    // order-major src[q][c][z][nb_pad] (centres in sorted order) -> dst[crow[c]][z][b][q]
+    const int nbp = nb_pad(nb);
+    const int64_t total = (int64_t)len * nc * nz * nb;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t q = t % len, rs = t / len;
-        const int64_t r = rs / sub, j = rs % sub;
-        dst[((int64_t)crow[r] * sub + j) * len + q] = src[rs * stride + q];
+        const int b = (int)(t % nb);
+        int64_t r = t / nb;
+        const int z = (int)(r % nz);
+        r /= nz;
+        const int64_t c = r % nc;
+        const int q = (int)(r / nc);
+        dst[(((int64_t)crow[c] * nz + z) * nb + b) * len + q] = src[(((int64_t)q * nc + c) * nz + z) * nbp + b];
     }
 }
 
@@ -589,8 +593,8 @@ static mp3pcf_status accumulate_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq,
     if (nc == 0) return MP3PCF_OK;
 
     // ---- stage (a)
-    MP3_CK(ctx->G.ensure(sizeof(cx<T>) * (size_t)nc * nz * nb * g_stride(c.n_max)));
-    MP3_CK(ctx->W.ensure(sizeof(cx<T>) * (size_t)nc * nz * nb * w_stride(c.n_max)));
+    MP3_CK(ctx->G.ensure(sizeof(cx<T>) * (size_t)(2 * c.n_max + 3) * nc * nz * nb_pad(nb)));
+    MP3_CK(ctx->W.ensure(sizeof(cx<T>) * (size_t)(2 * c.n_max + 1) * nc * nz * nb_pad(nb)));
     MomentArgs<T> a;
     a.n_centres = nc;
     a.centre_idx = ctx->centre_idx.as<int>();
@@ -655,15 +659,14 @@ mp3pcf_status mp3pcf_copy_moments(mp3pcf_ctx* ctx, void* d_G, void* d_W)
     const int64_t nc = ctx->n_centres;
     if (nc == 0) return MP3PCF_OK;
     const mp3pcf_config& c = ctx->cfg;
-    const int sub = c.n_z * c.n_bins, lg = 2 * c.n_max + 3, lw = 2 * c.n_max + 1;
-    const int sg = g_stride(c.n_max), sw = w_stride(c.n_max);
-    const unsigned gr = grid1d(nc * sub * lg, ctx->n_sm);
+    const int nz = c.n_z, nb = c.n_bins, lg = 2 * c.n_max + 3, lw = 2 * c.n_max + 1;
+    const unsigned gr = grid1d(nc * nz * nb * lg, ctx->n_sm);
     if (ctx->fp64) {
-        if (d_G) k_copy_rows<double><<<gr, 256, 0, ctx->st>>>(nc, sub, lg, sg, ctx->crow.as<int>(), ctx->G.as<cx<double>>(), (cx<double>*)d_G);
-        if (d_W) k_copy_rows<double><<<gr, 256, 0, ctx->st>>>(nc, sub, lw, sw, ctx->crow.as<int>(), ctx->W.as<cx<double>>(), (cx<double>*)d_W);
+        if (d_G) k_copy_rows<double><<<gr, 256, 0, ctx->st>>>(nc, nz, nb, lg, ctx->crow.as<int>(), ctx->G.as<cx<double>>(), (cx<double>*)d_G);
+        if (d_W) k_copy_rows<double><<<gr, 256, 0, ctx->st>>>(nc, nz, nb, lw, ctx->crow.as<int>(), ctx->W.as<cx<double>>(), (cx<double>*)d_W);
     } else {
-        if (d_G) k_copy_rows<float><<<gr, 256, 0, ctx->st>>>(nc, sub, lg, sg, ctx->crow.as<int>(), ctx->G.as<cx<float>>(), (cx<float>*)d_G);
-        if (d_W) k_copy_rows<float><<<gr, 256, 0, ctx->st>>>(nc, sub, lw, sw, ctx->crow.as<int>(), ctx->W.as<cx<float>>(), (cx<float>*)d_W);
+        if (d_G) k_copy_rows<float><<<gr, 256, 0, ctx->st>>>(nc, nz, nb, lg, ctx->crow.as<int>(), ctx->G.as<cx<float>>(), (cx<float>*)d_G);
+        if (d_W) k_copy_rows<float><<<gr, 256, 0, ctx->st>>>(nc, nz, nb, lw, ctx->crow.as<int>(), ctx->W.as<cx<float>>(), (cx<float>*)d_W);
     }
     MP3_CK(cudaGetLastError());
     return MP3PCF_OK;

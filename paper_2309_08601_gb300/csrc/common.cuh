@@ -89,8 +89,8 @@ struct MomentArgs {
     GridDesc g;
     int32_t nz, nb, n_max;
     const long long* e2q;       // [nb + 1] exact squared edges in fixed-point units^2
-    cx<T>* G;                   // [n_centres][nz][nb][g_stride(n_max)]
-    cx<T>* W;                   // [n_centres][nz][nb][w_stride(n_max)]
+    cx<T>* G;                   // [2 n_max + 3][n_centres][nz][nb_pad(nb)]
+    cx<T>* W;                   // [2 n_max + 1][n_centres][nz][nb_pad(nb)]
     unsigned long long* pairs;  // [0] pair counter, [1] error flags (1: a bounded wait gave up)
 };
 
@@ -141,10 +141,12 @@ cudaError_t launch_to_map3(const PostArgs& p, const double* gcen, int n_ap, cons
 
 __host__ __device__ inline int groups_per_zt(int n_max) { return 4 * (n_max + 1) + 2 * n_max + 1; }
 
-// row strides (complex elements) of the moment arrays in device memory: the 2 n_max + 3 orders
-// of G and the 2 n_max + 1 orders of W, each padded by one element so that a row is a multiple
-// of 16 bytes (a requirement of tensor-memory-access copies); the pad is never written or used
-__host__ __device__ inline int g_stride(int n_max) { return 2 * n_max + 4; }
-__host__ __device__ inline int w_stride(int n_max) { return 2 * n_max + 2; }
+// The moment arrays in device memory are order-major: element (order slot q, centre c, Z z,
+// bin b) at ((q * n_centres + c) * nz + z) * nb_pad(nb) + b, the bins padded to an even count so
+// that a (q, c, z) row is a multiple of 16 bytes. A group of consecutive orders over a range of
+// centres is then a few long contiguous rows (what the tensor-memory-access copies and coalesced
+// loads want). Order slots: G q = m + n_max + 3 (m = -n_max-3..n_max-1), W q = m (m = 0..2 n_max).
+// The pad bin is never written and never used.
+__host__ __device__ inline int nb_pad(int nb) { return (nb + 1) & ~1; }
 
 }  // namespace mp3

@@ -43,8 +43,9 @@ __global__ void __launch_bounds__(kThreads) contract_kernel(const ContractArgs<T
         case 3: mx = n - 3; my = n - 1; yconj = true; break;      // G_{n-3} G_{n-1}^*
         default: mx = n; my = n; yconj = true; break;             // W_n W_n^*
     }
-    const int M = kind < 4 ? g_stride(n_max) : w_stride(n_max);
     const int off = kind < 4 ? n_max + 3 : 0;
+    const int nbp = nb_pad(nb);
+    const size_t plane = (size_t)a.n_centres * nz * nbp;  // stride between order slots
     const cx<T>* src = kind < 4 ? a.G : a.W;
     const int nbb = nb * nb;
     const int per = (a.n_centres + a.splits - 1) / a.splits;
@@ -73,8 +74,8 @@ __global__ void __launch_bounds__(kThreads) contract_kernel(const ContractArgs<T
                     } else {
                         coef = cx<T>{-pv.a, -pv.b};  // -(w gamma)
                     }
-                    X = src[(((size_t)c * nz + z2) * nb + b) * M + mx + off];
-                    Y = src[(((size_t)c * nz + z3) * nb + b) * M + my + off];
+                    X = src[(size_t)(mx + off) * plane + ((size_t)c * nz + z2) * nbp + b];
+                    Y = src[(size_t)(my + off) * plane + ((size_t)c * nz + z3) * nbp + b];
                     if (xconj) X = cconj(X);
                     if (yconj) Y = cconj(Y);
                     X = cmul(coef, X);

@@ -143,17 +143,18 @@ struct TcArgs {
     int groups;   // nz^3 * groups_per_zt(n_max): index space of the partial sums
     int gt;       // groups per tile
     int npad;     // MMA N: gt * 2 nb rounded up to 16
-    int bw;       // orders per TMA box (even, >= gt + 1)
+    int nbp;      // bins padded to even (the moment rows)
     int ta, tw;   // tiles per component of Upsilon (n_max + 1 orders) and of N (2 n_max + 1 orders)
     unsigned long long* err;
 };
 
-// TMA boxes of one raw slot: X moments [KT][nb][bw] complex, Y moments (same), coefficients [KT]
+// TMA boxes of one raw slot: X moments [gt orders][KT centres][nbp bins] complex, Y moments
+// (same), coefficients [KT]
 struct RawLayout {
     int box_bytes, slot_bytes;
-    __host__ __device__ RawLayout(int kt, int nb, int bw)
+    __host__ __device__ RawLayout(int kt, int nbp, int gt)
     {
-        box_bytes = kt * nb * bw * 8;
+        box_bytes = gt * kt * nbp * 8;
         slot_bytes = ((2 * box_bytes + kt * 16) + 127) / 128 * 128;
     }
 };
@@ -179,17 +180,18 @@ struct Layout {
 constexpr int kRaw = 3;  // raw slots: the TMA copies run two stages ahead of the conversion
 
 template <class SP>
-static size_t smem_bytes(int kt, int nb, int bw, int gt)
+static size_t smem_bytes(int kt, int nb, int nbp, int gt)
 {
-    const RawLayout R(kt, nb, bw);
-    return (size_t)kRaw * R.slot_bytes + kStages * (size_t)Layout<SP>::STAGE_BYTES + (size_t)gt * nb * nb * sizeof(float2);
+    const RawLayout R(kt, nbp, gt);
+    return (size_t)kRaw * R.slot_bytes + kStages * (size_t)Layout<SP>::STAGE_BYTES + (size_t)gt * 4 * nb * nb * sizeof(float);
 }
 
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar)
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, int w,
+                                            uint32_t bar)
 {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
         : "memory");
 }
 
@@ -233,9 +235,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// barriers among the converter warps only (named barrier 1); every converter thread reaches each
-// of them, also after an abort, so none can wait for a warp that left
-__device__ __forceinline__ void conv_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConvWarps * 32) : "memory"); }
+// agreement among the converter warps only (named barrier 1); every converter thread reaches
+// each of them, also after an abort, so none can wait for a warp that left
 
 __device__ __forceinline__ bool conv_all(bool v)
 {
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(kThreads, 2) contract_tc_kernel(const __grid_c
     const ContractArgs<float>& A = a.c;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nb = A.nb, nz = A.nz, n_max = A.n_max;
-    const int nbb = nb * nb, nb2 = 2 * nb, bw = a.bw;
+    const int nbb = nb * nb, nb2 = 2 * nb, nbp = a.nbp;
 
     // ---- the tile: Z-triplet, component, first order, number of groups
     const int per_tile_zt = 4 * a.ta + a.tw;
@@ -302,10 +303,9 @@ __global__ void __launch_bounds__(kThreads, 2) contract_tc_kernel(const __grid_c
         default: ax = n0; sx = 1; ay = n0; sy = 1; break;            // W_n W_n^*
     }
     const int off = kind < 4 ? n_max + 3 : 0;
-    // first element of each box: the lowest order index, rounded down to an even element so the
-    // box starts on a 16-byte boundary
-    const int ix0 = ((sx > 0 ? ax : ax - (ng - 1)) + off) & ~1;
-    const int iy0 = ((sy > 0 ? ay : ay - (ng - 1)) + off) & ~1;
+    // first order slot of each box: the lowest one of the tile
+    const int ix0 = (sx > 0 ? ax : ax - (ng - 1)) + off;
+    const int iy0 = (sy > 0 ? ay : ay - (ng - 1)) + off;
     const CUtensorMap* mapM = kind < 4 ? &mapG : &mapW;
 
     const int sl = blockIdx.y, slices = gridDim.y;
@@ -314,10 +314,11 @@ __global__ void __launch_bounds__(kThreads, 2) contract_tc_kernel(const __grid_c
     const int ntiles = (c1 - c0 + KT - 1) / KT;
     const int nchains = (ntiles + kFlush - 1) / kFlush;
 
-    const RawLayout R(KT, nb, bw);
+    const RawLayout R(KT, nbp, a.gt);
     unsigned char* raw = smem;
     unsigned char* ops = smem + kRaw * R.slot_bytes;
-    float2* dacc = reinterpret_cast<float2*>(ops + kStages * L::STAGE_BYTES);  // [ng][nb][nb] (re, im)
+    // FP32 sums of the diagonal blocks: dq[gc][ri] = D[row of group gc / nb2, ri][gc], gc < ng nb2
+    float* dq = reinterpret_cast<float*>(ops + kStages * L::STAGE_BYTES);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -345,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, 2) contract_tc_kernel(const __grid_c
     // zero the operand stages (rows outside the stacked groups stay zero) and the block sums
     {
         uint4* z = reinterpret_cast<uint4*>(ops);
-        const int n16 = (kStages * L::STAGE_BYTES + ng * nbb * 8 + 15) / 16;
+        const int n16 = (kStages * L::STAGE_BYTES + ng * 4 * nbb * 4 + 15) / 16;
         for (int i = tid; i < n16; i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -366,8 +367,8 @@ __global__ void __launch_bounds__(kThreads, 2) contract_tc_kernel(const __grid_c
                 const uint32_t bar = smem_u32(&rawfull[slot]);
                 const int cb = c0 + s * KT;
                 mbar_expect_tx(bar, tx_bytes);
-                tma_load_3d(dst, mapM, 2 * ix0, z2 * nb, cb, bar);
-                tma_load_3d(dst + R.box_bytes, mapM, 2 * iy0, z3 * nb, cb, bar);
+                tma_load_4d(dst, mapM, 0, z2, cb, ix0, bar);
+                tma_load_4d(dst + R.box_bytes, mapM, 0, z3, cb, iy0, bar);
                 tma_load_2d(dst + 2 * R.box_bytes, &mapC, 0, cb, bar);
                 last_tma = s + 1;
             }
@@ -423,64 +424,50 @@ __global__ void __launch_bounds__(kThreads, 2) contract_tc_kernel(const __grid_c
             const int kw_lo = it & 3, rest = it >> 2;
             const int tb = rest % TB, kw = (rest / TB) * 4 + kw_lo;
             const int t = tb / nb, b = tb % nb;
-            const int ox = ax + sx * t + off - ix0, oy = ay + sy * t + off - iy0;  // order offset in the box
+            const int ox = ax + sx * t + off - ix0, oy = ay + sy * t + off - iy0;  // order plane in the box
             const int rre = t * nb2 + b;
             i_ore[q] = L::word_off(rre, kw);
             i_oim[q] = L::word_off(rre + nb, kw);
             i_k[q] = it < items ? kw * PK : 1 << 20;  // first centre of the word; out of range: no item
-            i_xo[q] = (kw * PK * nb + b) * bw + ox;   // complex index in the X box
-            i_yo[q] = (kw * PK * nb + b) * bw + oy;
+            i_xo[q] = (ox * KT + kw * PK) * nbp + b;  // complex index in the X box
+            i_yo[q] = (oy * KT + kw * PK) * nbp + b;
         }
         // L = coef X with coef = -(w gamma), -(w gamma)^* or w; conjugations as signs
         const float ca = kind == 4 ? 0.f : -1.f, cw = kind == 4 ? 1.f : 0.f;
         const float cb_ = kind == 4 ? 0.f : (kind == 1 ? 1.f : -1.f);
         const float xs = kind == 2 ? -1.f : 1.f, ys = kind >= 3 ? -1.f : 1.f;
         const float fz1 = (float)z1;
-        // TMEM lane quarter and column half this warp reads; the accumulator row it holds
-        const int quarter = warp & 3, half = warp >> 2;
+        // TMEM lane quarter and column part this warp reads; the accumulator row it holds
+        constexpr int kParts = kConvWarps / 4;
+        const int quarter = warp & 3, part = warp >> 2;
         const int row = quarter * 32 + lane;
         const int rt = row / nb2, ri = row % nb2;
-        const bool re_row = ri < nb;
-        const int b1 = re_row ? ri : ri - nb;
-        const int ncol = a.npad / 2, colb = half * ncol;
+        const int ncol = a.npad / kParts, colb = part * ncol;  // ncol: a multiple of 8
+        // the columns of this row's diagonal block inside this warp's part
+        const int qlo = rt < ng ? max(0, rt * nb2 - colb) : 0;
+        const int qhi = rt < ng ? min(ncol, rt * nb2 + nb2 - colb) : 0;
 
-        // adds chain c's accumulator to dacc (Re rows, then Im rows: one writer per element and
-        // phase) and hands the accumulator back to the MMA warp
+        // adds chain c's accumulator to dq (every element has one writer: its row's thread) and
+        // hands the accumulator back to the MMA warp; 16 columns at a time, loads before stores
         auto flush = [&](int c, bool go) -> bool {
             if (go) go = wait_or_abort(smem_u32(&accfull[c & 1]), (c >> 1) & 1, &abort_flag, a.err);
             if (!conv_all(go)) return false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((c & 1) * kTmemCols);
-            for (int phase = 0; phase < 2; ++phase) {
-                const bool mine = rt < ng && re_row == (phase == 0);
-                float2* D = dacc + (rt * nb + b1) * nb;
-                for (int col = colb; col < colb + ncol; col += 8) {
-                    uint32_t v[8];
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                                   "=r"(v[6]), "=r"(v[7])
-                                 : "r"(base + (uint32_t)col));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (mine) {
+            const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((c & 1) * kTmemCols + colb);
+            for (int q0 = 0; q0 < ncol; q0 += 8) {
+                uint32_t v[8];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                               "=r"(v[6]), "=r"(v[7])
+                             : "r"(base + (uint32_t)q0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float* d = dq + (colb + q0) * nb2 + ri;  // column colb + q0 + j at d[j * nb2]
+                float o[8];
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const int j = col + q - rt * nb2;
-                            if (j >= 0 && j < nb2) {
-                                const float x = __uint_as_float(v[q]);
-                                const bool re_col = j < nb;
-                                float2* e = D + (re_col ? j : j - nb);
-                                if (re_row) {
-                                    if (re_col) e->x += x;  // Re L Re R
-                                    else e->y += x;         // Re L Im R
-                                } else {
-                                    if (re_col) e->y += x;  // Im L Re R
-                                    else e->x -= x;         // - Im L Im R
-                                }
-                            }
-                        }
-                    }
-                }
-                conv_sync();
+                for (int j = 0; j < 8; ++j) o[j] = (q0 + j >= qlo && q0 + j < qhi) ? d[j * nb2] : 0.f;
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (q0 + j >= qlo && q0 + j < qhi) d[j * nb2] = o[j] + __uint_as_float(v[j]);
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
@@ -510,7 +497,7 @@ __global__ void __launch_bounds__(kThreads, 2) contract_tc_kernel(const __grid_c
                     for (int p = 0; p < PK; ++p) {
                         const int k = i_k[q] + p;
                         const float4 cf = rc[k];
-                        float2 X = rx[i_xo[q] + p * nb * bw], Y = ry[i_yo[q] + p * nb * bw];
+                        float2 X = rx[i_xo[q] + p * nbp], Y = ry[i_yo[q] + p * nbp];
                         const bool use = k < kend && cf.w == fz1;
                         const float cr = ca * cf.x + cw * cf.z, ci = cb_ * cf.y;
                         X.y *= xs;
@@ -580,13 +567,19 @@ __global__ void __launch_bounds__(kThreads, 2) contract_tc_kernel(const __grid_c
             mbar_wait(smem_u32(&opempty[(last_mma - 1) % kStages]), ((last_mma - 1) / kStages) & 1, a.err);
         __syncthreads();
     }
-    // the complex block sums, in FP64
+    // the complex block sums, in FP64: (Re L Re R - Im L Im R, Re L Im R + Im L Re R)
     for (int it = tid; it < ng * nbb; it += kThreads) {
-        const float2 v = ok ? dacc[it] : make_float2(0.f, 0.f);
-        const int t = it / nbb, o = it % nbb;
+        const int t = it / nbb, o = it % nbb, b1 = o / nb, b2 = o % nb;
+        double re = 0.0, im = 0.0;
+        if (ok) {
+            const float* Dre = dq + (t * nb2 + b2) * nb2;       // column Re R(b2)
+            const float* Dim = dq + (t * nb2 + nb + b2) * nb2;  // column Im R(b2)
+            re = (double)Dre[b1] - (double)Dim[nb + b1];
+            im = (double)Dim[b1] + (double)Dre[nb + b1];
+        }
         double* dst = A.partial + 2 * (((size_t)sl * a.groups + (gbase + t)) * nbb + o);
-        dst[0] = (double)v.x;
-        dst[1] = (double)v.y;
+        dst[0] = re;
+        dst[1] = im;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -646,13 +639,13 @@ static EncodeTiledFn encode_fn()
     return fn;
 }
 
-// FP32 tensor of rank 2 or 3 (dims innermost first, strides in bytes of dims 1..), boxes as given
+// FP32 tensor of rank 2 to 4 (dims innermost first, strides in bytes of dims 1..), boxes as given
 static bool encode(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
                    const uint32_t* box)
 {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
-    const cuuint32_t es[3] = {1, 1, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<void*>(base), dims, strides, box, es,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -662,7 +655,7 @@ template <class SP>
 static cudaError_t launch_tc(TcArgs a, float4* coef, int n_sm, int* splits_out, bool plan_only, cudaStream_t st)
 {
     const ContractArgs<float>& c = a.c;
-    const size_t smem = smem_bytes<SP>(SP::KT, c.nb, a.bw, a.gt);
+    const size_t smem = smem_bytes<SP>(SP::KT, c.nb, a.nbp, a.gt);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -676,18 +669,18 @@ static cudaError_t launch_tc(TcArgs a, float4* coef, int n_sm, int* splits_out, 
     if (plan_only) return cudaSuccess;
     if (slices != c.splits) return cudaErrorInvalidValue;  // partial buffer sized for another plan
 
-    // tensor maps: moments [n_centres][nz * nb][stride] complex as FP32 (innermost first)
-    const uint64_t rows = (uint64_t)c.nz * c.nb, nc = (uint64_t)c.n_centres;
-    const uint64_t sg = g_stride(c.n_max), sw = w_stride(c.n_max);
-    const uint32_t box[3] = {(uint32_t)(2 * a.bw), (uint32_t)c.nb, (uint32_t)SP::KT};
+    // tensor maps: order-major moments [orders][n_centres][nz][nbp] complex as FP32 (innermost first)
+    const uint64_t nbp = (uint64_t)a.nbp, nz = (uint64_t)c.nz, nc = (uint64_t)c.n_centres;
+    const uint32_t box[4] = {(uint32_t)(2 * nbp), 1u, (uint32_t)SP::KT, (uint32_t)a.gt};
+    const uint64_t strides[3] = {nbp * 8, nz * nbp * 8, nc * nz * nbp * 8};
     CUtensorMap mg, mw, mc;
     {
-        const uint64_t d[3] = {2 * sg, rows, nc}, s[2] = {sg * 8, rows * sg * 8};
-        if (!encode(&mg, c.G, 3, d, s, box)) return cudaErrorInvalidValue;
+        const uint64_t d[4] = {2 * nbp, nz, nc, (uint64_t)(2 * c.n_max + 3)};
+        if (!encode(&mg, c.G, 4, d, strides, box)) return cudaErrorInvalidValue;
     }
     {
-        const uint64_t d[3] = {2 * sw, rows, nc}, s[2] = {sw * 8, rows * sw * 8};
-        if (!encode(&mw, c.W, 3, d, s, box)) return cudaErrorInvalidValue;
+        const uint64_t d[4] = {2 * nbp, nz, nc, (uint64_t)(2 * c.n_max + 1)};
+        if (!encode(&mw, c.W, 4, d, strides, box)) return cudaErrorInvalidValue;
     }
     {
         const uint64_t d[2] = {4, nc}, s[1] = {16};
@@ -711,7 +704,7 @@ cudaError_t launch_contract_tc(const ContractArgs<float>& c, bool tf32, int n_sm
     a.gt = std::min(tc::kMaxGroups, tc::kM / (2 * c.nb));
     if (a.gt < 1) return cudaErrorInvalidValue;
     a.npad = ((a.gt * 2 * c.nb + 15) / 16) * 16;
-    a.bw = (a.gt + 2) & ~1;
+    a.nbp = nb_pad(c.nb);
     a.ta = (c.n_max + 1 + a.gt - 1) / a.gt;
     a.tw = (2 * c.n_max + 1 + a.gt - 1) / a.gt;
     a.err = err;

@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(MomPlan<T, NMAX>::NT, MomPlan<T, NMAX>::MINB) 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int nb = A.nb, nz = A.nz, n_max = A.n_max;
-    const int MG = g_stride(n_max), MW = w_stride(n_max);  // padded row strides
+    const size_t plane = (size_t)A.n_centres * nz * nb_pad(nb);  // stride between order slots
     const float S = (float)A.g.side, iS = 1.0f / S;
     // the last order slot of this warp may fall outside the order range
     const bool lastW = warp + (NWM - 1) * P <= 2 * NMAX;
@@ -422,16 +422,16 @@ __global__ void __launch_bounds__(MomPlan<T, NMAX>::NT, MomPlan<T, NMAX>::MINB) 
 #pragma unroll
                 for (int i = 0; i < PER; ++i) st[lane * PER + i] = acc[i];
                 __syncwarp();
-                const size_t row = ((size_t)c * nz + z) * nb + b;
-                cx<T>* Gp = A.G + row * MG;
-                cx<T>* Wp = A.W + row * MW;
+                const size_t row = ((size_t)c * nz + z) * nb_pad(nb) + b;
+                cx<T>* Gp = A.G + row;  // order slot q at Gp[q * plane]
+                cx<T>* Wp = A.W + row;
                 if (lane < NWM) {
                     const int j = lane, m = warp + j * P;
-                    if (m <= 2 * n_max) Wp[m] = cx<T>{st[4 * NABM + 2 * j], st[4 * NABM + 2 * j + 1]};
+                    if (m <= 2 * n_max) Wp[m * plane] = cx<T>{st[4 * NABM + 2 * j], st[4 * NABM + 2 * j + 1]};
                     if (j < NABM) {
                         const T ax = st[4 * j], ay = st[4 * j + 1], bx = st[4 * j + 2], by = st[4 * j + 3];
-                        if (m <= n_max - 1) Gp[m + n_max + 3] = cx<T>{ax - by, ay + bx};
-                        if (m >= 1 && m <= n_max + 3) Gp[n_max + 3 - m] = cx<T>{ax + by, bx - ay};
+                        if (m <= n_max - 1) Gp[(m + n_max + 3) * plane] = cx<T>{ax - by, ay + bx};
+                        if (m >= 1 && m <= n_max + 3) Gp[(n_max + 3 - m) * plane] = cx<T>{ax + by, bx - ay};
                     }
                 }
                 __syncwarp();
