@@ -45,7 +45,7 @@ HBM_PEAK_GBS = _measured_hbm_gbs()
 # workload: ncu capture at 50 000 galaxies (profiles/moments_kernel_lognormal_50k.md) scaled to
 # 200 000 centres (the traffic is the G/W write, proportional to the number of centres).
 # Set to None whenever the kernel changes until it is captured again.
-MOMENTS_TRAFFIC_BYTES = 4 * (12.030976e6 + 934.902784e6)
+MOMENTS_TRAFFIC_BYTES = None  # the kernel's output layout changed since the last capture
 
 
 def flops_per_pair(n_max: int) -> int:
@@ -193,6 +193,32 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ multi-rank host logic
+
+def rank_seed(seed: int, rank: int) -> int:
+    """Catalog seed of a rank: every rank measures its own independent realisation (weak scaling)."""
+    return seed + 1000 * rank
+
+
+def reduce_over_ranks(values, op: str, dist=None):
+    """Reduces a list of floats over the process group ('max' or 'sum'); identity on one rank.
+    NCCL groups reduce on the current CUDA device, gloo groups on the host."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    dev = torch.device("cpu")
+    if dist.get_backend() == "nccl":
+        dev = torch.device("cuda", torch.cuda.current_device())
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op={"max": dist.ReduceOp.MAX, "sum": dist.ReduceOp.SUM}[op])
+    return [float(v) for v in t.cpu()]
+
+
+def whole_job(units_per_step_all_ranks: float, steps: int, seconds_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_step_all_ranks * steps / seconds_max
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_gpu(args):
@@ -217,7 +243,7 @@ def run_gpu(args):
     native.lib()
 
     p, setup, theta = workload_setup(args.workload, args.n)
-    cat = synth.make_catalog(p["n"], p["side"], p["seed"] + 1000 * rank, field=p["field"],
+    cat = synth.make_catalog(p["n"], p["side"], rank_seed(p["seed"], rank), field=p["field"],
                              weights=p["weights"], holes=p.get("holes", False))
     dev = api.catalog_to_device(cat)
     stream = torch.cuda.current_stream()
@@ -253,13 +279,11 @@ def run_gpu(args):
     ms = ev0.elapsed_time(ev1)
     stages = est.stage_times(reset=True)
     est.set_timing(False)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = reduce_over_ranks([ms], "max", dist)[0]
+    pairs_all = reduce_over_ranks([pairs], "sum", dist)[0]  # each rank has its own catalog
     sec = ms_max / 1e3
-    value = world * args.steps * pairs / sec
-    cat_per_s = world * args.steps / sec
+    value = whole_job(pairs_all, args.steps, sec)
+    cat_per_s = whole_job(world, args.steps, sec)
 
     # ---- roofline of the dominant kernel (stage a, FP32 FMA pipe)
     k1_ms = stages["moments"][0] / args.steps
@@ -269,7 +293,7 @@ def run_gpu(args):
                 "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                 "traffic": (args.k1_traffic if args.k1_traffic is not None else
                             (MOMENTS_TRAFFIC_BYTES if (args.workload == "lognormal_200k" and not args.n
-                                                       and args.precision == "fp32") else None)),
+                                                       and args.precision != "fp64") else None)),
                 "traffic_note": "ncu DRAM read+write, capture at 50 000 galaxies scaled by centres",
                 "flops_per_pair": fpp, "pairs_per_launch": pairs,
                 "launch_ms": k1_ms, "peak_source": PEAK_NOTE}
@@ -302,11 +326,8 @@ def run_gpu(args):
         out_host.copy_(m.m8, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_s = float(te.item())
-    e2e = {"value": world * args.steps * pairs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+    e2e_s = reduce_over_ranks([e2e_s], "max", dist)[0]
+    e2e = {"value": whole_job(pairs_all, args.steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
     m8_fp32 = m.m8.cpu().numpy()
@@ -363,7 +384,9 @@ def main(argv=None):
     ap.add_argument("--workload", default="lognormal_200k")
     ap.add_argument("--n", type=int, default=0,
                     help="rescale the workload to n galaxies at the same density (profiling runs)")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16x3", "tf32x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp32", "fp64"],
+                    help="bf16x3 (default): FP32 moments, BF16 hi+lo tensor-core contraction, FP64 "
+                         "edge correction and sums")
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work sampled")
