@@ -156,6 +156,45 @@ mp3pcf_status mp3pcf_to_gamma(mp3pcf_ctx* ctx, const double* d_gamma_n, int32_t 
 mp3pcf_status mp3pcf_to_map3(mp3pcf_ctx* ctx, const double* d_gamma_cen, int64_t n_ap,
                              const double* d_theta_ap, double* d_corr, double* d_m8);
 
+/* ---- Adjoints (reverse mode), the differentiation form: dL/d(gamma_1, gamma_2, w) for a real
+ * loss L of the aperture measures, by the chain to_map3 -> to_gamma -> edge_correct ->
+ * contract_multipoles -> accumulate_moments taken backwards. For every complex quantity z the
+ * gradient is grad z = dL/dRe z + i dL/dIm z (interleaved complex double, like the forward
+ * buffers). All are stream-ordered and allocation happens only in the context's workspace. */
+
+/* dL/dGamma^cen [n_z^3][4][n_bins][n_bins][n_phi] (OVERWRITTEN) of the aperture integral and
+ * 8-measure combination (Sec. 5.2, App. C, Eqs. MapTrafo8_1-8) for apertures d_theta_ap
+ * [n_ap][3], from d_grad_corr [n_z^3][n_ap][4] complex and/or d_grad_m8 [n_z^3][n_ap][8]
+ * (either may be NULL; both NULL gives zeros). */
+mp3pcf_status mp3pcf_to_map3_adjoint(mp3pcf_ctx* ctx, int64_t n_ap, const double* d_theta_ap,
+                                     const double* d_grad_corr, const double* d_grad_m8,
+                                     double* d_grad_gamma_cen);
+
+/* dL/dGamma_n [n_z^3][4][2 n_max+1][n_bins][n_bins] (OVERWRITTEN) from
+ * d_grad_gamma_phi [n_z^3][4][n_bins][n_bins][n_phi] of mp3pcf_to_gamma with the same projection
+ * (the multipole sum and, for projection 1, the centroid factors). */
+mp3pcf_status mp3pcf_to_gamma_adjoint(mp3pcf_ctx* ctx, int32_t projection, const double* d_grad_gamma_phi,
+                                      double* d_grad_gamma_n);
+
+/* dL/dUpsilon [n_z^3][4][n_max+1][n_bins][n_bins] and dL/dN [n_z^3][2 n_max+1][n_bins][n_bins]
+ * (both OVERWRITTEN) of the edge-correction solve (Eqs. ModeCoupling, GammaMultipolesWithEC):
+ * per system Y = A^{-H} dL/dGamma, dL/dA = -Y Gamma^H folded along the Toeplitz diagonals and
+ * through the App. A symmetries. d_norm and d_gamma_n are the forward N and its solution; systems
+ * that were singular contribute zeros. */
+mp3pcf_status mp3pcf_edge_correct_adjoint(mp3pcf_ctx* ctx, const double* d_norm, const double* d_gamma_n,
+                                          const double* d_grad_gamma_n, double* d_grad_upsilon,
+                                          double* d_grad_norm);
+
+/* Adjoint of mp3pcf_contract_multipoles and mp3pcf_accumulate_moments for the catalog of the
+ * LAST accumulate call (the context still holds its sorted copy and moments): ADDS dL/dgamma_1,
+ * dL/dgamma_2 and dL/dw per galaxy, in the caller's order, to d_grad_g1, d_grad_g2, d_grad_w
+ * (float [n]; any may be NULL) given dL/dUpsilon and dL/dN. n and d_g1, d_g2, d_w must be the
+ * catalog of that call (EINVAL if n differs). Arithmetic in the forward moment precision; the
+ * scatter to neighbours uses atomics, so the result is not bit-reproducible. */
+mp3pcf_status mp3pcf_moments_adjoint(mp3pcf_ctx* ctx, const double* d_grad_upsilon, const double* d_grad_norm,
+                                     int64_t n, const float* d_g1, const float* d_g2, const float* d_w,
+                                     float* d_grad_g1, float* d_grad_g2, float* d_grad_w);
+
 /* Tracing. With timing on, every stage call records a pair of CUDA events on the context
  * stream around its kernels. mp3pcf_stage_times returns, per stage, the accumulated device time
  * in ms (h_ms[6], may be NULL) and the number of kernel launches (h_launches[6], may be NULL;

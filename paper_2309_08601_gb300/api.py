@@ -113,6 +113,7 @@ class Estimator:
 
     # ------------------------------------------------------------------ stage (a)
     def accumulate_moments(self, xq, yq, g1, g2, w, zbin=None, centre_mask=None):
+        self._generation = getattr(self, "_generation", 0) + 1
         torch = _torch()
         n = int(xq.numel())
         _need(xq, torch.int32, "xq", n)
@@ -190,6 +191,56 @@ class Estimator:
                                                  _ptr(corr), _ptr(m8)), "mp3pcf_to_map3", self._ctx)
         return corr, m8
 
+    # ------------------------------------------------------------------ adjoints
+    def to_map3_adjoint(self, theta_ap, grad_m8=None, grad_corr=None):
+        """dL/dGamma^cen from dL/dm8 and/or dL/dcorr (complex gradients: dL/dRe + i dL/dIm)."""
+        torch = _torch()
+        th = torch.as_tensor(np.atleast_2d(np.asarray(theta_ap, dtype=np.float64)),
+                             device=self.device).contiguous()
+        n_ap = th.shape[0]
+        if grad_m8 is not None:
+            grad_m8 = _need(grad_m8.contiguous(), torch.float64, "grad_m8", self.z3 * n_ap * 8)
+        if grad_corr is not None:
+            grad_corr = _need(grad_corr.contiguous(), torch.complex128, "grad_corr", self.z3 * n_ap * 4)
+        out = torch.empty((self.z3, 4, self.n_bins, self.n_bins, self.cfg.n_phi),
+                          dtype=torch.complex128, device=self.device)
+        native.check(native.lib().mp3pcf_to_map3_adjoint(self._ctx, n_ap, _ptr(th), _ptr(grad_corr),
+                                                         _ptr(grad_m8), _ptr(out)),
+                     "mp3pcf_to_map3_adjoint", self._ctx)
+        return out
+
+    def to_gamma_adjoint(self, grad_gamma_phi, projection: int):
+        torch = _torch()
+        g = _need(grad_gamma_phi.contiguous(), torch.complex128, "grad_gamma_phi")
+        out = torch.empty((self.z3, 4, 2 * self.n_max + 1, self.n_bins, self.n_bins),
+                          dtype=torch.complex128, device=self.device)
+        native.check(native.lib().mp3pcf_to_gamma_adjoint(self._ctx, int(projection), _ptr(g), _ptr(out)),
+                     "mp3pcf_to_gamma_adjoint", self._ctx)
+        return out
+
+    def edge_correct_adjoint(self, norm, gamma_n, grad_gamma_n):
+        """(dL/dUpsilon, dL/dN) of the edge-correction solve."""
+        torch = _torch()
+        g = _need(grad_gamma_n.contiguous(), torch.complex128, "grad_gamma_n")
+        gu, gn = self.new_multipoles()
+        native.check(native.lib().mp3pcf_edge_correct_adjoint(self._ctx, _ptr(norm), _ptr(gamma_n), _ptr(g),
+                                                              _ptr(gu), _ptr(gn)),
+                     "mp3pcf_edge_correct_adjoint", self._ctx)
+        return gu, gn
+
+    def moments_adjoint(self, grad_ups, grad_norm, g1, g2, w):
+        """(dL/dgamma_1, dL/dgamma_2, dL/dw) per galaxy for the catalog of the last
+        accumulate_moments call, given dL/dUpsilon and dL/dN."""
+        torch = _torch()
+        n = g1.numel()
+        for t, nm in ((g1, "g1"), (g2, "g2"), (w, "w")):
+            _need(t, torch.float32, nm, n)
+        out = [torch.zeros(n, dtype=torch.float32, device=self.device) for _ in range(3)]
+        native.check(native.lib().mp3pcf_moments_adjoint(
+            self._ctx, _ptr(grad_ups.contiguous()), _ptr(grad_norm.contiguous()), n, _ptr(g1), _ptr(g2),
+            _ptr(w), _ptr(out[0]), _ptr(out[1]), _ptr(out[2])), "mp3pcf_moments_adjoint", self._ctx)
+        return tuple(out)
+
     # ------------------------------------------------------------------ tracing
     STAGES = ("sort", "moments", "contract", "edge_correct", "to_gamma", "to_map3")
 
@@ -227,3 +278,53 @@ def catalog_to_device(cat, device=None):
             torch.as_tensor(np.ascontiguousarray(cat.g1, np.float32), device=dev),
             torch.as_tensor(np.ascontiguousarray(cat.g2, np.float32), device=dev),
             torch.as_tensor(np.ascontiguousarray(cat.w, np.float32), device=dev), zb)
+
+
+# ---------------------------------------------------------------------- differentiation form
+
+def _map3_function():
+    torch = _torch()
+
+    class Map3Function(torch.autograd.Function):
+        """m8 = Map^3 measures of a catalog, differentiable in (gamma_1, gamma_2, w) through the
+        library's hand-written adjoint kernels. The forward keeps the catalog's moments in the
+        estimator's context; if the context has been used for another catalog before backward
+        runs, the moments are recomputed from the saved inputs first."""
+
+        @staticmethod
+        def forward(ctx, g1, g2, w, est, xq, yq, theta_ap, zbin, centre_mask):
+            m = est.measure(xq, yq, g1, g2, w, theta_ap, zbin, centre_mask, report_singular=False)
+            ctx.est, ctx.theta = est, theta_ap
+            ctx.geom = (xq, yq, zbin, centre_mask)
+            ctx.generation = est._generation
+            ctx.save_for_backward(g1, g2, w, m.norm, m.gamma_n)
+            return m.m8
+
+        @staticmethod
+        def backward(ctx, grad_m8):
+            g1, g2, w, norm, gam = ctx.saved_tensors
+            est = ctx.est
+            xq, yq, zbin, cmask = ctx.geom
+            if est._generation != ctx.generation:
+                est.accumulate_moments(xq, yq, g1, g2, w, zbin, cmask)  # recompute G, W
+                ctx.generation = est._generation
+            ggc = est.to_map3_adjoint(ctx.theta, grad_m8=grad_m8.to(torch.float64))
+            ggn = est.to_gamma_adjoint(ggc, 1)
+            gu, gn = est.edge_correct_adjoint(norm, gam, ggn)
+            d1, d2, dw = est.moments_adjoint(gu, gn, g1.detach(), g2.detach(), w.detach())
+            return d1, d2, dw, None, None, None, None, None, None
+
+    return Map3Function
+
+
+_MAP3_FN = None
+
+
+def map3(est, xq, yq, g1, g2, w, theta_ap, zbin=None, centre_mask=None):
+    """Differentiable <Map^3> measures m8 [n_z^3][n_ap][8] (float64) of a catalog: backward gives
+    dL/dgamma_1, dL/dgamma_2, dL/dw (float32, per galaxy) through the library's adjoint kernels
+    (to_map3 -> to_gamma -> edge_correct -> contraction -> moments, all on the GPU)."""
+    global _MAP3_FN
+    if _MAP3_FN is None:
+        _MAP3_FN = _map3_function()
+    return _MAP3_FN.apply(g1, g2, w, est, xq, yq, theta_ap, zbin, centre_mask)

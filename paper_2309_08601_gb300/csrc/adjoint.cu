@@ -1,0 +1,442 @@
+// Adjoint (reverse mode) of stages (b) and (a): given dL/dUpsilon and dL/dN for a real loss L,
+// the gradient with respect to every galaxy's w gamma and w (paper Sec. 3.1: Eqs.
+// Upsilon0_Derivation, Upsilon1-3, 3PCF_Normalization, tomoGn for (b); the moment sums of
+// Sec. 3.1 for (a)).
+//
+// Convention: for a complex quantity z, grad z = dL/dRe z + i dL/dIm z. For y = a z,
+// grad z += conj(a) grad y; for y = a conj(z), grad z += a conj(grad y); for a real parameter t in
+// y = t h, dL/dt += Re(conj(grad y) h).
+//
+// Stage (b), per group (Z-triplet, component, n) with y(b1, b2) = sum_i c_i X_i(b1) Y_i(b2):
+//   grad X_i(b1) = conj(c_i) sum_b2 grad y(b1, b2) conj(Y_i(b2)),
+//   grad Y_i(b2) = conj(c_i) sum_b1 grad y(b1, b2) conj(X_i(b1)),
+//   grad c_i     = sum_b1 conj(X_i(b1)) sum_b2 grad y(b1, b2) conj(Y_i(b2)),
+// with an extra conjugation where the moment enters conjugated. dL/dG and dL/dW are gathered per
+// output moment element (each written once, no atomics): an element receives the X or Y role of
+// at most eight (component, n) groups.
+//
+// Stage (a): G_m(i, b) = sum_k v_k e^{i m phi_ik} and W_m(i, b) = sum_k w_k e^{i m phi_ik}, so
+//   grad v_k += sum_{i, m} grad G_m(i, b_ik) e^{-i m phi_ik},
+//   dL/dw_k  += Re sum_{i, m} grad W_m(i, b_ik) e^{-i m phi_ik}.
+// For each (centre, bin) the adjoint moments are the coefficients of a trigonometric polynomial
+// evaluated at every neighbour's angle by Horner's rule (in u = e^{-i phi} for m >= 0 and in
+// z = e^{i phi} for m < 0), one neighbour per lane, and added to the neighbour's gradient with
+// atomics (the gradient is therefore not bit-reproducible). Neighbours are found per bin from
+// the cell grid of the forward pass: for every cell row, the one or two runs of cells that meet
+// the annulus.
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace mp3 {
+
+namespace adj {
+
+template <typename T>
+__device__ __forceinline__ cx<T> ld(const cx<T>* p, size_t i)
+{
+    return p[i];
+}
+
+__device__ __forceinline__ cx<double> ldd(const double* p, size_t i)
+{
+    return cx<double>{p[2 * i], p[2 * i + 1]};
+}
+
+template <typename T>
+__device__ __forceinline__ cx<T> to_t(cx<double> v)
+{
+    return cx<T>{(T)v.x, (T)v.y};
+}
+
+template <typename T>
+__device__ __forceinline__ void cfma(cx<T>& acc, cx<T> a, cx<T> b)
+{
+    acc.x += a.x * b.x - a.y * b.y;
+    acc.y += a.x * b.y + a.y * b.x;
+}
+
+// ------------------------------------------------------------------ stage (b): dL/dG, dL/dW
+
+constexpr int kTileC = 32;  // centres per block
+
+// grid: x = centre tiles, y = output order slot (G slots 0..MG-1, then W slots); thread per
+// (centre, z, bin) output element
+template <typename T>
+__global__ void __launch_bounds__(256) contract_adjoint_moments(const AdjArgs<T> a)
+{
+    const int nb = a.nb, nz = a.nz, nmax = a.n_max, nbp = nb_pad(nb);
+    const int MG = 2 * nmax + 3, o = nmax + 3, NN = nmax + 1, NW = 2 * nmax + 1;
+    const int q = blockIdx.y;
+    const bool isG = q < MG;
+    const int m = isG ? q - o : q - MG;
+    const size_t plane = (size_t)a.n_centres * nz * nbp;
+    for (int e = threadIdx.x; e < kTileC * nz * nb; e += blockDim.x) {
+        const int b = e % nb, z = (e / nb) % nz;
+        const int c = blockIdx.x * kTileC + e / (nb * nz);
+        if (c >= a.n_centres) continue;
+        const int d = a.centre_idx[c];
+        const Pay<T> pv = a.pay[d];
+        const int z1 = a.zs ? (int)a.zs[d] : 0;
+        const cx<T> v{pv.a, pv.b};
+        const cx<T> c0{-v.x, -v.y}, c1{-v.x, v.y};  // -v and -conj(v)
+        const cx<T> cw{pv.w, T(0)};
+        const size_t crow = (size_t)c * nz;
+        // X role: output at b1 = b, partner Y at order slot qy of Z zo; returns
+        // conj(coef) sum_b2 grad y(b, b2) conj(Y(b2))
+        auto roleX = [&](const cx<T>* M, const double* gy, size_t gbase, int zo, int qy, bool yconj, cx<T> coef) {
+            cx<T> s{T(0), T(0)};
+            const cx<T>* Y = M + (size_t)qy * plane + (crow + zo) * nbp;
+            for (int b2 = 0; b2 < nb; ++b2) {
+                cx<T> y = Y[b2];
+                if (!yconj) y.y = -y.y;  // conj(Y) (conj(conj(G)) = G when Y enters conjugated)
+                cfma(s, to_t<T>(ldd(gy, gbase + (size_t)b * nb + b2)), y);
+            }
+            return cmul(s, cconj(coef));
+        };
+        // Y role: output at b2 = b, partner X at order slot qx of Z zo
+        auto roleY = [&](const cx<T>* M, const double* gy, size_t gbase, int zo, int qx, bool xconj, cx<T> coef) {
+            cx<T> s{T(0), T(0)};
+            const cx<T>* X = M + (size_t)qx * plane + (crow + zo) * nbp;
+            for (int b1 = 0; b1 < nb; ++b1) {
+                cx<T> x = X[b1];
+                if (!xconj) x.y = -x.y;
+                cfma(s, to_t<T>(ldd(gy, gbase + (size_t)b1 * nb + b)), x);
+            }
+            return cmul(s, cconj(coef));
+        };
+        auto ub = [&](int zt, int kind, int n) { return ((((size_t)zt * 4 + kind) * NN + n) * nb) * nb; };
+        cx<T> acc{T(0), T(0)};
+        if (isG) {
+            for (int zo = 0; zo < nz; ++zo) {
+                const int ztX = (z1 * nz + z) * nz + zo;  // this element as X (Z2 = z), partner Z3 = zo
+                const int ztY = (z1 * nz + zo) * nz + z;  // this element as Y (Z3 = z), partner Z2 = zo
+                int n;
+                // kind 0: G_{n-3}(b1) G_{-n-3}(b2), coef -v
+                n = m + 3;
+                if (n >= 0 && n <= nmax) acc = cadd(acc, roleX(a.G, a.gups, ub(ztX, 0, n), zo, -n - 3 + o, false, c0));
+                n = -m - 3;
+                if (n >= 0 && n <= nmax) acc = cadd(acc, roleY(a.G, a.gups, ub(ztY, 0, n), zo, n - 3 + o, false, c0));
+                // kind 1: G_{n-1}(b1) G_{-n-1}(b2), coef -conj(v)
+                n = m + 1;
+                if (n >= 0 && n <= nmax) acc = cadd(acc, roleX(a.G, a.gups, ub(ztX, 1, n), zo, -n - 1 + o, false, c1));
+                n = -m - 1;
+                if (n >= 0 && n <= nmax) acc = cadd(acc, roleY(a.G, a.gups, ub(ztY, 1, n), zo, n - 1 + o, false, c1));
+                // kind 2: conj(G_{-n-1}(b1)) G_{-n-3}(b2), coef -v
+                n = -m - 1;
+                if (n >= 0 && n <= nmax)
+                    acc = cadd(acc, cconj(roleX(a.G, a.gups, ub(ztX, 2, n), zo, -n - 3 + o, false, c0)));
+                n = -m - 3;
+                if (n >= 0 && n <= nmax) acc = cadd(acc, roleY(a.G, a.gups, ub(ztY, 2, n), zo, -n - 1 + o, true, c0));
+                // kind 3: G_{n-3}(b1) conj(G_{n-1}(b2)), coef -v
+                n = m + 3;
+                if (n >= 0 && n <= nmax) acc = cadd(acc, roleX(a.G, a.gups, ub(ztX, 3, n), zo, n - 1 + o, true, c0));
+                n = m + 1;
+                if (n >= 0 && n <= nmax)
+                    acc = cadd(acc, cconj(roleY(a.G, a.gups, ub(ztY, 3, n), zo, n - 3 + o, false, c0)));
+            }
+            a.gG[(size_t)q * plane + (crow + z) * nbp + b] = acc;
+        } else {
+            const int n = m;
+            for (int zo = 0; zo < nz; ++zo) {
+                const int ztX = (z1 * nz + z) * nz + zo, ztY = (z1 * nz + zo) * nz + z;
+                // N_n: w W_n(b1) conj(W_n(b2))
+                const size_t nX = (((size_t)ztX * NW + n) * nb) * nb, nY = (((size_t)ztY * NW + n) * nb) * nb;
+                acc = cadd(acc, roleX(a.W, a.gnorm, nX, zo, n, true, cw));
+                acc = cadd(acc, cconj(roleY(a.W, a.gnorm, nY, zo, n, false, cw)));
+            }
+            a.gW[(size_t)n * plane + (crow + z) * nbp + b] = acc;
+        }
+    }
+}
+
+// grad of every centre's own coefficient: thread per centre, the group's dL/dy staged in shared
+// memory; adds dL/dv (re, im) and dL/dw of the centre's sorted galaxy
+template <typename T>
+__global__ void __launch_bounds__(128) contract_adjoint_coef(const AdjArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* gy = reinterpret_cast<cx<T>*>(smem_raw);  // [nb][nb]
+    const int nb = a.nb, nz = a.nz, nmax = a.n_max, nbp = nb_pad(nb);
+    const int o = nmax + 3, NN = nmax + 1, NW = 2 * nmax + 1;
+    const int per_zt = groups_per_zt(nmax);
+    const size_t plane = (size_t)a.n_centres * nz * nbp;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = c < a.n_centres;
+    const int d = act ? a.centre_idx[c] : 0;
+    const int zc = act && a.zs ? (int)a.zs[d] : 0;
+    cx<T> gv{T(0), T(0)};
+    T gw = T(0);
+    const int groups = nz * nz * nz * per_zt;
+    for (int g = 0; g < groups; ++g) {
+        const int zt = g / per_zt, loc = g % per_zt;
+        const int z1 = zt / (nz * nz), z2 = (zt / nz) % nz, z3 = zt % nz;
+        int kind, n;
+        if (loc < 4 * NN) {
+            kind = loc / NN;
+            n = loc % NN;
+        } else {
+            kind = 4;
+            n = loc - 4 * NN;
+        }
+        const double* src = kind < 4 ? a.gups + 2 * ((((size_t)zt * 4 + kind) * NN + n) * nb * nb)
+                                      : a.gnorm + 2 * (((size_t)zt * NW + n) * nb * nb);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nb * nb; i += blockDim.x) gy[i] = cx<T>{(T)src[2 * i], (T)src[2 * i + 1]};
+        __syncthreads();
+        if (!act || zc != z1) continue;
+        int qx, qy;
+        bool xc = false, yc = false;
+        switch (kind) {
+            case 0: qx = n - 3 + o; qy = -n - 3 + o; break;
+            case 1: qx = n - 1 + o; qy = -n - 1 + o; break;
+            case 2: qx = -n - 1 + o; qy = -n - 3 + o; xc = true; break;
+            case 3: qx = n - 3 + o; qy = n - 1 + o; yc = true; break;
+            default: qx = n; qy = n; yc = true; break;
+        }
+        const cx<T>* M = kind < 4 ? a.G : a.W;
+        const cx<T>* X = M + (size_t)qx * plane + ((size_t)c * nz + z2) * nbp;
+        const cx<T>* Y = M + (size_t)qy * plane + ((size_t)c * nz + z3) * nbp;
+        // gc = sum_b1 conj(X(b1)) sum_b2 gy(b1, b2) conj(Y(b2))
+        cx<T> gc{T(0), T(0)};
+        for (int b1 = 0; b1 < nb; ++b1) {
+            cx<T> s{T(0), T(0)};
+            for (int b2 = 0; b2 < nb; ++b2) {
+                cx<T> y = Y[b2];
+                if (!yc) y.y = -y.y;
+                cfma(s, gy[b1 * nb + b2], y);
+            }
+            cx<T> x = X[b1];
+            if (!xc) x.y = -x.y;
+            cfma(gc, x, s);
+        }
+        if (kind == 4) {
+            gw += gc.x;  // c = w
+        } else if (kind == 1) {
+            gv.x -= gc.x;  // c = -conj(v): grad v = -conj(grad c)
+            gv.y += gc.y;
+        } else {
+            gv.x -= gc.x;  // c = -v
+            gv.y -= gc.y;
+        }
+    }
+    if (act) {
+        a.gv[2 * (size_t)d] += gv.x;
+        a.gv[2 * (size_t)d + 1] += gv.y;
+        a.gw[d] += gw;
+    }
+}
+
+// ------------------------------------------------------------------ stage (a): pair loop
+
+__device__ __forceinline__ long long isqrt_floor(long long v)
+{
+    if (v <= 0) return 0;
+    long long r = (long long)sqrt((double)v);
+    while (r * r > v) --r;
+    while ((r + 1) * (r + 1) <= v) ++r;
+    return r;
+}
+
+__device__ __forceinline__ long long fdiv(long long a, long long b)
+{
+    const long long q = a / b;
+    return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
+}
+
+template <typename T>
+__device__ __forceinline__ void atomic_add_t(T* p, T v);
+template <>
+__device__ __forceinline__ void atomic_add_t<float>(float* p, float v)
+{
+    atomicAdd(p, v);
+}
+template <>
+__device__ __forceinline__ void atomic_add_t<double>(double* p, double v)
+{
+    atomicAdd(p, v);
+}
+
+template <typename T>
+__device__ __forceinline__ cx<T> unit_dir(long long dx, long long dy);
+template <>
+__device__ __forceinline__ cx<float> unit_dir<float>(long long dx, long long dy)
+{
+    const float fx = (float)dx, fy = (float)dy;
+    const float ir = rsqrtf(fx * fx + fy * fy);
+    return {fx * ir, fy * ir};
+}
+template <>
+__device__ __forceinline__ cx<double> unit_dir<double>(long long dx, long long dy)
+{
+    const double fx = (double)dx, fy = (double)dy;
+    const double ir = 1.0 / sqrt(fx * fx + fy * fy);
+    return {fx * ir, fy * ir};
+}
+
+constexpr int kPairWarps = 4;
+
+// warp per centre (grid-stride); per bin the warp stages the centre's adjoint moments of every Z
+// in shared memory and walks the annulus
+template <typename T>
+__global__ void __launch_bounds__(kPairWarps * 32) moments_adjoint_pairs(const AdjArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nb = a.nb, nz = a.nz, nmax = a.n_max, nbp = nb_pad(nb);
+    const int MG = 2 * nmax + 3, MW = 2 * nmax + 1, o = nmax + 3;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cx<T>* co = reinterpret_cast<cx<T>*>(smem_raw) + (size_t)warp * nz * (MG + MW);  // [z][MG + MW]
+    const size_t plane = (size_t)a.n_centres * nz * nbp;
+    const GridDesc g = a.g;
+    for (int c = blockIdx.x * kPairWarps + warp; c < a.n_centres; c += gridDim.x * kPairWarps) {
+        const int d = a.centre_idx[c];
+        const int2 p = a.pos[d];
+        const long long px = p.x, py = p.y;
+        for (int b = 0; b < nb; ++b) {
+            __syncwarp();
+            for (int i = lane; i < nz * (MG + MW); i += 32) {
+                const int z = i / (MG + MW), qq = i % (MG + MW);
+                co[i] = qq < MG ? a.gG[(size_t)qq * plane + ((size_t)c * nz + z) * nbp + b]
+                                : a.gW[(size_t)(qq - MG) * plane + ((size_t)c * nz + z) * nbp + b];
+            }
+            __syncwarp();
+            const long long r2lo = a.e2q[b], r2hi = a.e2q[b + 1];  // in bin: r2lo <= r2 < r2hi
+            const long long R = isqrt_floor(r2hi - 1);
+            const long long ya = max(0LL, fdiv(py - R - g.y0, g.side));
+            const long long yb = min((long long)g.ncy - 1, fdiv(py + R - g.y0, g.side));
+            for (long long yy = ya; yy <= yb; ++yy) {
+                const long long ylo = g.y0 + yy * g.side, yhi = ylo + g.side - 1;
+                const long long dymin = max(0LL, max(ylo - py, py - yhi));
+                const long long dymax = max(llabs(ylo - py), llabs(yhi - py));
+                if (dymin * dymin > r2hi - 1) continue;
+                const long long dxo = isqrt_floor(r2hi - 1 - dymin * dymin);
+                long long ca = fdiv(px - dxo - g.x0, g.side), cb = fdiv(px + dxo - g.x0, g.side);
+                if (cb < 0 || ca > g.ncx - 1) continue;
+                ca = max(ca, 0LL);
+                cb = min(cb, (long long)g.ncx - 1);
+                // cells wholly inside the inner radius (every point at r^2 < r2lo) are skipped
+                long long cl = cb + 1, cr = cb;
+                if (r2lo - 1 - dymax * dymax >= 0) {
+                    const long long hx = isqrt_floor(r2lo - 1 - dymax * dymax);
+                    cl = -fdiv(-(px - hx - g.x0), g.side);        // first cell starting at >= px - hx
+                    cr = fdiv(px + hx - g.x0 + 1, g.side) - 1;    // last cell ending at <= px + hx
+                }
+                long long segs[2][2];
+                int nseg = 0;
+                if (cl <= cr && cl <= cb && cr >= ca) {
+                    if (ca <= cl - 1) { segs[nseg][0] = ca; segs[nseg][1] = cl - 1; ++nseg; }
+                    if (cr + 1 <= cb) { segs[nseg][0] = cr + 1; segs[nseg][1] = cb; ++nseg; }
+                } else {
+                    segs[0][0] = ca;
+                    segs[0][1] = cb;
+                    nseg = 1;
+                }
+                for (int z = 0; z < nz; ++z) {
+                    const cx<T>* gg = co + (size_t)z * (MG + MW);
+                    const cx<T>* gw = gg + MG;
+                    for (int sgi = 0; sgi < nseg; ++sgi) {
+                        const size_t key0 = (size_t)z * g.ncells + (size_t)yy * g.ncx;
+                        const int k0 = a.cell_start[key0 + segs[sgi][0]];
+                        const int k1 = a.cell_start[key0 + segs[sgi][1] + 1];
+                        for (int k = k0 + lane; k < k1; k += 32) {
+                            const int2 qk = a.pos[k];
+                            const long long dx = (long long)qk.x - px, dy = (long long)qk.y - py;
+                            const long long r2 = dx * dx + dy * dy;
+                            if (r2 < r2lo || r2 >= r2hi) continue;
+                            const cx<T> zz = unit_dir<T>(dx, dy);
+                            const cx<T> u{zz.x, -zz.y};
+                            // m >= 0 part of sum_m gG_m u^m (Horner in u)
+                            cx<T> P{T(0), T(0)};
+                            for (int mm = nmax - 1; mm >= 0; --mm) {
+                                P = cmul(P, u);
+                                P = cadd(P, gg[o + mm]);
+                            }
+                            // m < 0 part: sum_{j >= 1} gG_{-j} z^j (Horner in z)
+                            cx<T> Q{T(0), T(0)};
+                            for (int j = nmax + 3; j >= 1; --j) {
+                                Q = cadd(Q, gg[o - j]);
+                                Q = cmul(Q, zz);
+                            }
+                            // W: sum_m gW_m u^m
+                            cx<T> Rw{T(0), T(0)};
+                            for (int mm = 2 * nmax; mm >= 0; --mm) {
+                                Rw = cmul(Rw, u);
+                                Rw = cadd(Rw, gw[mm]);
+                            }
+                            atomic_add_t<T>(&a.gv[2 * (size_t)k], P.x + Q.x);
+                            atomic_add_t<T>(&a.gv[2 * (size_t)k + 1], P.y + Q.y);
+                            atomic_add_t<T>(&a.gw[k], Rw.x);
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+// caller order, v = w (gamma_1 + i gamma_2): dL/dgamma_1 = w Re grad v, dL/dgamma_2 = w Im grad v,
+// dL/dw = (direct) + Re grad v gamma_1 + Im grad v gamma_2; ADDS to the caller's arrays
+template <typename T>
+__global__ void adjoint_finish(int64_t n, const int* __restrict__ perm, const T* __restrict__ gv,
+                               const T* __restrict__ gw, const float* __restrict__ g1, const float* __restrict__ g2,
+                               const float* __restrict__ w, float* __restrict__ dg1, float* __restrict__ dg2,
+                               float* __restrict__ dw)
+{
+    for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < n; d += (int64_t)gridDim.x * blockDim.x) {
+        const int i = perm[d];
+        const T vr = gv[2 * d], vi = gv[2 * d + 1];
+        const T wi = (T)w[i];
+        if (dg1) dg1[i] += (float)(wi * vr);
+        if (dg2) dg2[i] += (float)(wi * vi);
+        if (dw) dw[i] += (float)(gw[d] + vr * (T)g1[i] + vi * (T)g2[i]);
+    }
+}
+
+template <typename T>
+static cudaError_t run(const AdjArgs<T>& a, int64_t n, const int* perm, const float* g1, const float* g2,
+                       const float* w, float* dg1, float* dg2, float* dw, int n_sm, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(a.gv, 0, sizeof(T) * 2 * (size_t)n, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.gw, 0, sizeof(T) * (size_t)n, st);
+    if (e != cudaSuccess) return e;
+    if (a.n_centres > 0) {
+        const int MG = 2 * a.n_max + 3, MW = 2 * a.n_max + 1;
+        dim3 g1d((a.n_centres + kTileC - 1) / kTileC, MG + MW);
+        contract_adjoint_moments<T><<<g1d, 256, 0, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const size_t sm_coef = sizeof(cx<T>) * (size_t)a.nb * a.nb;
+        e = cudaFuncSetAttribute(contract_adjoint_coef<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_coef);
+        if (e != cudaSuccess) return e;
+        contract_adjoint_coef<T><<<(a.n_centres + 127) / 128, 128, sm_coef, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const size_t sm_pair = sizeof(cx<T>) * (size_t)kPairWarps * a.nz * (MG + MW);
+        e = cudaFuncSetAttribute(moments_adjoint_pairs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_pair);
+        if (e != cudaSuccess) return e;
+        const int blocks = (int)std::min<int64_t>((a.n_centres + kPairWarps - 1) / kPairWarps, (int64_t)n_sm * 32);
+        moments_adjoint_pairs<T><<<blocks, kPairWarps * 32, sm_pair, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)n_sm * 16));
+    adjoint_finish<T><<<gb, 256, 0, st>>>(n, perm, a.gv, a.gw, g1, g2, w, dg1, dg2, dw);
+    return cudaGetLastError();
+}
+
+}  // namespace adj
+
+cudaError_t launch_moments_adjoint_f32(const AdjArgs<float>& a, int64_t n, const int* perm, const float* g1,
+                                       const float* g2, const float* w, float* dg1, float* dg2, float* dw,
+                                       int n_sm, cudaStream_t st)
+{
+    return adj::run<float>(a, n, perm, g1, g2, w, dg1, dg2, dw, n_sm, st);
+}
+
+cudaError_t launch_moments_adjoint_f64(const AdjArgs<double>& a, int64_t n, const int* perm, const float* g1,
+                                       const float* g2, const float* w, float* dg1, float* dg2, float* dw,
+                                       int n_sm, cudaStream_t st)
+{
+    return adj::run<double>(a, n, perm, g1, g2, w, dg1, dg2, dw, n_sm, st);
+}
+
+}  // namespace mp3

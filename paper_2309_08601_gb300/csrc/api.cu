@@ -298,6 +298,7 @@ struct mp3pcf_ctx {
     DevBuf bb, key, count, fill, scan_sums, scan_total, perm, pos, pay, zs;
     DevBuf cflag, crank, oflag, orank, centre_idx, crow;
     DevBuf G, W, pairs, partial, singular, m3partial, ccoef;
+    DevBuf gG, gW, gv, gw, adjscratch;  // adjoint workspace
     // tracing: per-stage event pairs and kernel-launch counts
     bool timing = false;
     int64_t launches[6] = {0, 0, 0, 0, 0, 0};
@@ -453,7 +454,8 @@ mp3pcf_status mp3pcf_destroy(mp3pcf_ctx* ctx)
                       &ctx->pos, &ctx->pay, &ctx->zs, &ctx->cflag,
                       &ctx->crank, &ctx->oflag, &ctx->orank, &ctx->centre_idx, &ctx->crow,
                       &ctx->G, &ctx->W, &ctx->pairs, &ctx->partial, &ctx->singular,
-                      &ctx->m3partial, &ctx->ccoef};
+                      &ctx->m3partial, &ctx->ccoef, &ctx->gG, &ctx->gW, &ctx->gv, &ctx->gw,
+                      &ctx->adjscratch};
     for (DevBuf* b : bufs) b->release();
     for (auto& pr : ctx->ev) {
         cudaEventDestroy(pr.second.first);
@@ -790,6 +792,119 @@ mp3pcf_status mp3pcf_to_map3(mp3pcf_ctx* ctx, const double* d_gamma_cen, int64_t
     MP3_CK(launch_to_map3(post_args(ctx), d_gamma_cen, (int)n_ap, d_theta_ap,
                           ctx->m3partial.as<double>(), chunks, d_corr, d_m8, ctx->st));
     return MP3PCF_OK;
+}
+
+// ------------------------------------------------------------------ adjoints
+
+mp3pcf_status mp3pcf_to_map3_adjoint(mp3pcf_ctx* ctx, int64_t n_ap, const double* d_theta_ap,
+                                     const double* d_grad_corr, const double* d_grad_m8,
+                                     double* d_grad_gamma_cen)
+{
+    if (!ctx || !d_grad_gamma_cen || n_ap < 0 || n_ap > 65535 || (n_ap > 0 && !d_theta_ap))
+        return fail(ctx, MP3PCF_EINVAL, "bad argument");
+    ctx->err.clear();
+    const mp3pcf_config& c = ctx->cfg;
+    const size_t npts = (size_t)c.n_z * c.n_z * c.n_z * 4 * c.n_bins * c.n_bins * c.n_phi;
+    if (n_ap == 0 || (!d_grad_corr && !d_grad_m8)) {
+        MP3_CK(cudaMemsetAsync(d_grad_gamma_cen, 0, sizeof(double) * 2 * npts, ctx->st));
+        return MP3PCF_OK;
+    }
+    StageScope sc(ctx, ST_MAP3);
+    ctx->launches[ST_MAP3] += 1;
+    MP3_CK(launch_to_map3_adjoint(post_args(ctx), (int)n_ap, d_theta_ap, d_grad_corr, d_grad_m8,
+                                  d_grad_gamma_cen, ctx->st));
+    return MP3PCF_OK;
+}
+
+mp3pcf_status mp3pcf_to_gamma_adjoint(mp3pcf_ctx* ctx, int32_t projection, const double* d_grad_gamma_phi,
+                                      double* d_grad_gamma_n)
+{
+    if (!ctx || !d_grad_gamma_phi || !d_grad_gamma_n || (projection != 0 && projection != 1))
+        return fail(ctx, MP3PCF_EINVAL, "bad argument");
+    ctx->err.clear();
+    StageScope sc(ctx, ST_GAMMA);
+    ctx->launches[ST_GAMMA] += 1;
+    MP3_CK(launch_to_gamma_adjoint(post_args(ctx), d_grad_gamma_phi, projection, d_grad_gamma_n, ctx->st));
+    return MP3PCF_OK;
+}
+
+mp3pcf_status mp3pcf_edge_correct_adjoint(mp3pcf_ctx* ctx, const double* d_norm, const double* d_gamma_n,
+                                          const double* d_grad_gamma_n, double* d_grad_upsilon,
+                                          double* d_grad_norm)
+{
+    if (!ctx || !d_norm || !d_gamma_n || !d_grad_gamma_n || !d_grad_upsilon || !d_grad_norm)
+        return fail(ctx, MP3PCF_EINVAL, "null argument");
+    ctx->err.clear();
+    const PostArgs p = post_args(ctx);
+    MP3_CK(ctx->adjscratch.ensure(edge_correct_adjoint_scratch(p)));
+    StageScope sc(ctx, ST_EDGE);
+    ctx->launches[ST_EDGE] += 2;
+    MP3_CK(launch_edge_correct_adjoint(p, d_norm, d_gamma_n, d_grad_gamma_n, ctx->adjscratch.as<double>(),
+                                       d_grad_upsilon, d_grad_norm, ctx->st));
+    return MP3PCF_OK;
+}
+
+}  // extern "C"
+
+template <typename T>
+static mp3pcf_status moments_adjoint_t(mp3pcf_ctx* ctx, const double* gups, const double* gnorm, const float* g1,
+                                       const float* g2, const float* w, float* dg1, float* dg2, float* dw)
+{
+    const mp3pcf_config& c = ctx->cfg;
+    const int64_t n = ctx->n, nc = ctx->n_centres;
+    const int nz = c.n_z, nb = c.n_bins;
+    MP3_CK(ctx->gv.ensure(sizeof(T) * 2 * (size_t)std::max<int64_t>(n, 1)));
+    MP3_CK(ctx->gw.ensure(sizeof(T) * (size_t)std::max<int64_t>(n, 1)));
+    if (nc > 0) {
+        MP3_CK(ctx->gG.ensure(sizeof(cx<T>) * (size_t)(2 * c.n_max + 3) * nc * nz * nb_pad(nb)));
+        MP3_CK(ctx->gW.ensure(sizeof(cx<T>) * (size_t)(2 * c.n_max + 1) * nc * nz * nb_pad(nb)));
+    }
+    AdjArgs<T> a;
+    a.n_centres = (int32_t)nc;
+    a.nz = nz;
+    a.nb = nb;
+    a.n_max = c.n_max;
+    a.centre_idx = ctx->centre_idx.as<int>();
+    a.pos = ctx->pos.as<int2>();
+    a.pay = ctx->pay.as<Pay<T>>();
+    a.zs = nz > 1 ? ctx->zs.as<uint8_t>() : nullptr;
+    a.cell_start = ctx->count.as<int>();
+    a.g = ctx->grid;
+    a.e2q = ctx->d_e2q.as<long long>();
+    a.G = ctx->G.as<cx<T>>();
+    a.W = ctx->W.as<cx<T>>();
+    a.gups = gups;
+    a.gnorm = gnorm;
+    a.gG = ctx->gG.as<cx<T>>();
+    a.gW = ctx->gW.as<cx<T>>();
+    a.gv = ctx->gv.as<T>();
+    a.gw = ctx->gw.as<T>();
+    StageScope sc(ctx, ST_MOMENTS);
+    ctx->launches[ST_MOMENTS] += nc > 0 ? 4 : 1;
+    cudaError_t e;
+    if constexpr (sizeof(T) == 8)
+        e = launch_moments_adjoint_f64(a, n, ctx->perm.as<int>(), g1, g2, w, dg1, dg2, dw, ctx->n_sm, ctx->st);
+    else
+        e = launch_moments_adjoint_f32(a, n, ctx->perm.as<int>(), g1, g2, w, dg1, dg2, dw, ctx->n_sm, ctx->st);
+    MP3_CK(e);
+    return MP3PCF_OK;
+}
+
+extern "C" {
+
+mp3pcf_status mp3pcf_moments_adjoint(mp3pcf_ctx* ctx, const double* d_grad_upsilon, const double* d_grad_norm,
+                                     int64_t n, const float* d_g1, const float* d_g2, const float* d_w,
+                                     float* d_grad_g1, float* d_grad_g2, float* d_grad_w)
+{
+    if (!ctx || !d_grad_upsilon || !d_grad_norm) return fail(ctx, MP3PCF_EINVAL, "null argument");
+    ctx->err.clear();
+    if (n != ctx->n) return fail(ctx, MP3PCF_EINVAL, "n differs from the last accumulate call");
+    if (n == 0) return MP3PCF_OK;
+    if (!d_g1 || !d_g2 || !d_w) return fail(ctx, MP3PCF_EINVAL, "null catalog pointer");
+    if (ctx->fp64) return moments_adjoint_t<double>(ctx, d_grad_upsilon, d_grad_norm, d_g1, d_g2, d_w, d_grad_g1,
+                                                    d_grad_g2, d_grad_w);
+    return moments_adjoint_t<float>(ctx, d_grad_upsilon, d_grad_norm, d_g1, d_g2, d_w, d_grad_g1, d_grad_g2,
+                                    d_grad_w);
 }
 
 mp3pcf_status mp3pcf_set_timing(mp3pcf_ctx* ctx, int32_t on)

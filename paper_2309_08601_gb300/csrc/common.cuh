@@ -139,6 +139,45 @@ cudaError_t launch_to_map3(const PostArgs& p, const double* gcen, int n_ap, cons
                            double* partial, int chunks, double* corr, double* m8,
                            cudaStream_t st);
 
+// ------------------------------------------------------------------ adjoint of stages (b), (a)
+
+template <typename T>
+struct AdjArgs {
+    int32_t n_centres, nz, nb, n_max;
+    const int32_t* centre_idx;  // sorted position of each centre
+    const int2* pos;            // sorted fixed-point positions
+    const Pay<T>* pay;          // sorted (w gamma_1, w gamma_2, w)
+    const uint8_t* zs;          // sorted zbin (NULL: one bin)
+    const int32_t* cell_start;  // as in MomentArgs
+    GridDesc g;
+    const long long* e2q;
+    const cx<T>* G;             // forward moments (order-major)
+    const cx<T>* W;
+    const double* gups;         // dL/dUpsilon [z3][4][n_max+1][nb][nb] complex
+    const double* gnorm;        // dL/dN [z3][2n_max+1][nb][nb] complex
+    cx<T>* gG;                  // dL/dG, dL/dW (order-major, like G and W)
+    cx<T>* gW;
+    T* gv;                      // [n][2] dL/dv per sorted galaxy (v = w gamma)
+    T* gw;                      // [n] direct dL/dw per sorted galaxy
+};
+
+cudaError_t launch_moments_adjoint_f32(const AdjArgs<float>& a, int64_t n, const int* perm, const float* g1,
+                                       const float* g2, const float* w, float* dg1, float* dg2, float* dw,
+                                       int n_sm, cudaStream_t st);
+cudaError_t launch_moments_adjoint_f64(const AdjArgs<double>& a, int64_t n, const int* perm, const float* g1,
+                                       const float* g2, const float* w, float* dg1, float* dg2, float* dw,
+                                       int n_sm, cudaStream_t st);
+
+// adjoints of the FP64 stages (overwrite their outputs)
+cudaError_t launch_to_map3_adjoint(const PostArgs& p, int n_ap, const double* theta, const double* gcorr,
+                                   const double* gm8, double* ggcen, cudaStream_t st);
+cudaError_t launch_to_gamma_adjoint(const PostArgs& p, const double* gphi, int projection, double* ggam,
+                                    cudaStream_t st);
+cudaError_t launch_edge_correct_adjoint(const PostArgs& p, const double* norm, const double* gam,
+                                        const double* ggam, double* scratch, double* gups, double* gnorm,
+                                        cudaStream_t st);
+size_t edge_correct_adjoint_scratch(const PostArgs& p);
+
 __host__ __device__ inline int groups_per_zt(int n_max) { return 4 * (n_max + 1) + 2 * n_max + 1; }
 
 // The moment arrays in device memory are order-major: element (order slot q, centre c, Z z,

@@ -3,67 +3,21 @@
 // aperture-measure integrals (Sec. 5.2, App. C).
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace mp3 {
 
 // ------------------------------------------------------------------ c1: edge correction
 
-// Block per (Z-triplet, b1, b2). The (2 n_max + 1)^2 complex matrix N_{l-n} and the four
-// right-hand sides Upsilon_{mu,l} live in shared memory; Gaussian elimination with partial
-// pivoting (largest |pivot|, lowest row on ties), then back substitution by four warps.
-__global__ void __launch_bounds__(256) edge_correct_kernel(const PostArgs p, const double* __restrict__ ups,
-                                                           const double* __restrict__ norm,
-                                                           double* __restrict__ gam,
-                                                           unsigned long long* nsing)
+// Solves A X = B in shared memory for one system (D x D complex A, D x 4 complex B, both
+// overwritten; X in B): Gaussian elimination with partial pivoting (largest |pivot|, lowest row
+// on ties) by the whole block, back substitution by four warps. Returns true if a pivot was zero.
+__device__ bool block_solve4(cx<double>* A, cx<double>* B, int D, double* red_v, int* red_i, int* s_bad)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nmax = p.n_max, D = 2 * nmax + 1, nb = p.nb, nz = p.nz;
-    const int NN = nmax + 1, NW = 2 * nmax + 1;
-    cx<double>* A = reinterpret_cast<cx<double>*>(smem_raw);
-    cx<double>* B = A + (size_t)D * D;
-    __shared__ double red_v[256];
-    __shared__ int red_i[256];
-    __shared__ int s_bad;
-    const int sys = blockIdx.x;
-    const int b2 = sys % nb, b1 = (sys / nb) % nb, zt = sys / (nb * nb);
-    const int z1 = zt / (nz * nz), z2 = (zt / nz) % nz, z3 = zt % nz;
-    const int zsw = (z1 * nz + z3) * nz + z2;
     const int tid = threadIdx.x;
-    const cx<double>* U = reinterpret_cast<const cx<double>*>(ups);
-    const cx<double>* Nn = reinterpret_cast<const cx<double>*>(norm);
-
-    for (int idx = tid; idx < D * D; idx += blockDim.x) {
-        const int l = idx / D - nmax, nn = idx % D - nmax, m = l - nn;
-        cx<double> v{0.0, 0.0};
-        if (!(p.norm_truncate && (m > nmax || m < -nmax))) {
-            if (m >= 0)
-                v = Nn[(((size_t)zt * NW + m) * nb + b1) * nb + b2];
-            else
-                v = Nn[(((size_t)zsw * NW + (-m)) * nb + b2) * nb + b1];
-        }
-        A[idx] = v;
-    }
-    for (int idx = tid; idx < D * 4; idx += blockDim.x) {
-        const int l = idx / 4 - nmax, mu = idx % 4;
-        cx<double> v;
-        if (l >= 0) {
-            v = U[((((size_t)zt * 4 + mu) * NN + l) * nb + b1) * nb + b2];
-        } else {
-            const int mus = mu == 2 ? 3 : (mu == 3 ? 2 : mu);
-            v = U[((((size_t)zsw * 4 + mus) * NN + (-l)) * nb + b2) * nb + b1];
-        }
-        B[idx] = v;
-    }
-    if (tid == 0) s_bad = 0;
-    __syncthreads();
-    if (tid == 0) {
-        const cx<double> n0 = A[(size_t)nmax * D + nmax];
-        if (n0.x == 0.0 && n0.y == 0.0) s_bad = 1;
-    }
-    __syncthreads();
-
-    for (int k = 0; k < D && !s_bad; ++k) {
+    for (int k = 0; k < D && !*s_bad; ++k) {
         double best = -1.0;
         int bi = D;
         for (int r = k + tid; r < D; r += blockDim.x) {
@@ -92,7 +46,7 @@ __global__ void __launch_bounds__(256) edge_correct_kernel(const PostArgs p, con
         const bool zero = !(red_v[0] > 0.0);
         __syncthreads();
         if (zero) {
-            if (tid == 0) s_bad = 1;
+            if (tid == 0) *s_bad = 1;
             __syncthreads();
             break;
         }
@@ -124,7 +78,7 @@ __global__ void __launch_bounds__(256) edge_correct_kernel(const PostArgs p, con
         }
         __syncthreads();
     }
-    const bool bad = s_bad != 0;
+    const bool bad = *s_bad != 0;
     const int warp = tid >> 5, lane = tid & 31;
     if (!bad && warp < 4) {
         const int mu = warp;
@@ -147,6 +101,66 @@ __global__ void __launch_bounds__(256) edge_correct_kernel(const PostArgs p, con
         }
     }
     __syncthreads();
+    return bad;
+}
+
+// element (l, n) of the extended mode-coupling matrix of system (zt, b1, b2): N_{l-n}, with
+// N_{-m}(b1, b2) = N_m(b2, b1) of the Z2 <-> Z3 swapped triplet (App. A)
+__device__ __forceinline__ cx<double> coupling(const PostArgs& p, const cx<double>* Nn, int zt, int zsw, int b1,
+                                               int b2, int m)
+{
+    const int nb = p.nb, nmax = p.n_max, NW = 2 * nmax + 1;
+    if (p.norm_truncate && (m > nmax || m < -nmax)) return cx<double>{0.0, 0.0};
+    if (m >= 0) return Nn[(((size_t)zt * NW + m) * nb + b1) * nb + b2];
+    return Nn[(((size_t)zsw * NW + (-m)) * nb + b2) * nb + b1];
+}
+
+// Block per (Z-triplet, b1, b2). The (2 n_max + 1)^2 complex matrix N_{l-n} and the four
+// right-hand sides Upsilon_{mu,l} live in shared memory and are solved by block_solve4.
+__global__ void __launch_bounds__(256) edge_correct_kernel(const PostArgs p, const double* __restrict__ ups,
+                                                           const double* __restrict__ norm,
+                                                           double* __restrict__ gam,
+                                                           unsigned long long* nsing)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nmax = p.n_max, D = 2 * nmax + 1, nb = p.nb, nz = p.nz;
+    const int NN = nmax + 1;
+    cx<double>* A = reinterpret_cast<cx<double>*>(smem_raw);
+    cx<double>* B = A + (size_t)D * D;
+    __shared__ double red_v[256];
+    __shared__ int red_i[256];
+    __shared__ int s_bad;
+    const int sys = blockIdx.x;
+    const int b2 = sys % nb, b1 = (sys / nb) % nb, zt = sys / (nb * nb);
+    const int z1 = zt / (nz * nz), z2 = (zt / nz) % nz, z3 = zt % nz;
+    const int zsw = (z1 * nz + z3) * nz + z2;
+    const int tid = threadIdx.x;
+    const cx<double>* U = reinterpret_cast<const cx<double>*>(ups);
+    const cx<double>* Nn = reinterpret_cast<const cx<double>*>(norm);
+
+    for (int idx = tid; idx < D * D; idx += blockDim.x) {
+        const int l = idx / D - nmax, nn = idx % D - nmax;
+        A[idx] = coupling(p, Nn, zt, zsw, b1, b2, l - nn);
+    }
+    for (int idx = tid; idx < D * 4; idx += blockDim.x) {
+        const int l = idx / 4 - nmax, mu = idx % 4;
+        cx<double> v;
+        if (l >= 0) {
+            v = U[((((size_t)zt * 4 + mu) * NN + l) * nb + b1) * nb + b2];
+        } else {
+            const int mus = mu == 2 ? 3 : (mu == 3 ? 2 : mu);
+            v = U[((((size_t)zsw * 4 + mus) * NN + (-l)) * nb + b2) * nb + b1];
+        }
+        B[idx] = v;
+    }
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    if (tid == 0) {
+        const cx<double> n0 = A[(size_t)nmax * D + nmax];
+        if (n0.x == 0.0 && n0.y == 0.0) s_bad = 1;
+    }
+    __syncthreads();
+    const bool bad = block_solve4(A, B, D, red_v, red_i, &s_bad);
     cx<double>* out = reinterpret_cast<cx<double>*>(gam);
     for (int idx = tid; idx < D * 4; idx += blockDim.x) {
         const int nn = idx / 4, mu = idx % 4;
@@ -154,6 +168,136 @@ __global__ void __launch_bounds__(256) edge_correct_kernel(const PostArgs p, con
             bad ? cx<double>{nan(""), nan("")} : B[idx];
     }
     if (bad && tid == 0) atomicAdd(nsing, 1ULL);
+}
+
+// Adjoint of the solve A X = B of system (zt, b1, b2): Y = A^{-H} dL/dX (the gradient of the
+// right-hand sides) and, for the matrix, dL/dA_{ln} = -sum_mu Y_mu(l) conj(X_mu(n)), summed along
+// each diagonal j = l - n (A is Toeplitz in l - n). Per system the scratch holds Y [D][4] then the
+// diagonal sums [2D - 1] (j = -(D-1)..D-1). Systems that were singular get zeros.
+__global__ void __launch_bounds__(256) edge_correct_adjoint_kernel(const PostArgs p, const double* __restrict__ norm,
+                                                                   const double* __restrict__ gam,
+                                                                   const double* __restrict__ ggam,
+                                                                   double* __restrict__ scratch)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nmax = p.n_max, D = 2 * nmax + 1, nb = p.nb, nz = p.nz;
+    cx<double>* A = reinterpret_cast<cx<double>*>(smem_raw);
+    cx<double>* B = A + (size_t)D * D;
+    cx<double>* X = B + (size_t)D * 4;
+    __shared__ double red_v[256];
+    __shared__ int red_i[256];
+    __shared__ int s_bad;
+    const int sys = blockIdx.x;
+    const int b2 = sys % nb, b1 = (sys / nb) % nb, zt = sys / (nb * nb);
+    const int z1 = zt / (nz * nz), z2 = (zt / nz) % nz, z3 = zt % nz;
+    const int zsw = (z1 * nz + z3) * nz + z2;
+    const int tid = threadIdx.x;
+    const cx<double>* Nn = reinterpret_cast<const cx<double>*>(norm);
+    const cx<double>* Gm = reinterpret_cast<const cx<double>*>(gam);
+    const cx<double>* gG = reinterpret_cast<const cx<double>*>(ggam);
+    // A^H: element (l, n) = conj(A_{n l}) = conj(N_{n - l})
+    for (int idx = tid; idx < D * D; idx += blockDim.x) {
+        const int l = idx / D - nmax, nn = idx % D - nmax;
+        A[idx] = cconj(coupling(p, Nn, zt, zsw, b1, b2, nn - l));
+    }
+    for (int idx = tid; idx < D * 4; idx += blockDim.x) {
+        const int nn = idx / 4, mu = idx % 4;
+        const size_t at = ((((size_t)zt * 4 + mu) * D + nn) * nb + b1) * nb + b2;
+        B[idx] = gG[at];
+        X[idx] = Gm[at];
+    }
+    if (tid == 0) {
+        s_bad = 0;
+        const cx<double> n0 = A[(size_t)nmax * D + nmax];
+        if (n0.x == 0.0 && n0.y == 0.0) s_bad = 1;
+        for (int i = 0; i < D * 4 && !s_bad; ++i)
+            if (!(isfinite(X[i].x) && isfinite(X[i].y))) s_bad = 1;
+    }
+    __syncthreads();
+    const bool bad = block_solve4(A, B, D, red_v, red_i, &s_bad);
+    cx<double>* out = reinterpret_cast<cx<double>*>(scratch) + (size_t)sys * (D * 4 + 2 * D - 1);
+    for (int idx = tid; idx < D * 4; idx += blockDim.x) out[idx] = bad ? cx<double>{0.0, 0.0} : B[idx];
+    for (int j = -(D - 1) + tid; j <= D - 1; j += blockDim.x) {
+        double sr = 0.0, si = 0.0;
+        if (!bad) {
+            const int l0 = max(0, j), l1 = min(D - 1, D - 1 + j);
+            for (int l = l0; l <= l1; ++l) {
+                const int nn = l - j;
+                for (int mu = 0; mu < 4; ++mu) {
+                    const cx<double> t = cmul(B[l * 4 + mu], cconj(X[nn * 4 + mu]));
+                    sr -= t.x;
+                    si -= t.y;
+                }
+            }
+        }
+        out[D * 4 + (j + D - 1)] = cx<double>{sr, si};
+    }
+}
+
+// dL/dUpsilon [z3][4][n_max+1][nb][nb] and dL/dN [z3][2n_max+1][nb][nb] from the per-system
+// scratch: each stored element is read by its own system and, for orders >= 1, by the system of
+// the swapped triplet and transposed bins through the App. A symmetries.
+__global__ void edge_correct_adjoint_gather(const PostArgs p, const double* __restrict__ scratch,
+                                            double* __restrict__ gups, double* __restrict__ gnorm)
+{
+    const int nmax = p.n_max, D = 2 * nmax + 1, nb = p.nb, nz = p.nz, NN = nmax + 1, NW = 2 * nmax + 1;
+    const int z3 = nz * nz * nz;
+    const int per = D * 4 + 2 * D - 1;
+    const cx<double>* S = reinterpret_cast<const cx<double>*>(scratch);
+    const int64_t nu = (int64_t)z3 * 4 * NN * nb * nb, nn_ = (int64_t)z3 * NW * nb * nb;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nu + nn_;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (t < nu) {
+            const int b2 = (int)(t % nb), b1 = (int)((t / nb) % nb);
+            const int l = (int)((t / ((int64_t)nb * nb)) % NN);
+            const int mu = (int)((t / ((int64_t)nb * nb * NN)) % 4);
+            const int zt = (int)(t / ((int64_t)nb * nb * NN * 4));
+            const int z1 = zt / (nz * nz), zb = (zt / nz) % nz, zc = zt % nz;
+            const int zsw = (z1 * nz + zc) * nz + zb;
+            const int mus = mu == 2 ? 3 : (mu == 3 ? 2 : mu);
+            cx<double> v = S[((size_t)(zt * nb + b1) * nb + b2) * per + (l + nmax) * 4 + mu];
+            if (l >= 1) v = cadd(v, S[((size_t)(zsw * nb + b2) * nb + b1) * per + (-l + nmax) * 4 + mus]);
+            reinterpret_cast<cx<double>*>(gups)[t] = v;
+        } else {
+            const int64_t u = t - nu;
+            const int b2 = (int)(u % nb), b1 = (int)((u / nb) % nb);
+            const int m = (int)((u / ((int64_t)nb * nb)) % NW);
+            const int zt = (int)(u / ((int64_t)nb * nb * NW));
+            const int z1 = zt / (nz * nz), zb = (zt / nz) % nz, zc = zt % nz;
+            const int zsw = (z1 * nz + zc) * nz + zb;
+            cx<double> v{0.0, 0.0};
+            if (!(p.norm_truncate && m > nmax)) {
+                v = S[((size_t)(zt * nb + b1) * nb + b2) * per + D * 4 + (m + D - 1)];
+                if (m >= 1) v = cadd(v, S[((size_t)(zsw * nb + b2) * nb + b1) * per + D * 4 + (-m + D - 1)]);
+            }
+            reinterpret_cast<cx<double>*>(gnorm)[u] = v;
+        }
+    }
+}
+
+cudaError_t launch_edge_correct_adjoint(const PostArgs& p, const double* norm, const double* gam,
+                                        const double* ggam, double* scratch, double* gups, double* gnorm,
+                                        cudaStream_t st)
+{
+    const int D = 2 * p.n_max + 1;
+    const size_t smem = sizeof(cx<double>) * ((size_t)D * D + (size_t)D * 8);
+    cudaError_t e = cudaFuncSetAttribute(edge_correct_adjoint_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int systems = p.nz * p.nz * p.nz * p.nb * p.nb;
+    edge_correct_adjoint_kernel<<<systems, 256, smem, st>>>(p, norm, gam, ggam, scratch);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t total = (int64_t)p.nz * p.nz * p.nz * p.nb * p.nb * (4 * (p.n_max + 1) + 2 * p.n_max + 1);
+    edge_correct_adjoint_gather<<<(unsigned)std::min<int64_t>((total + 255) / 256, 65535), 256, 0, st>>>(
+        p, scratch, gups, gnorm);
+    return cudaGetLastError();
+}
+
+size_t edge_correct_adjoint_scratch(const PostArgs& p)
+{
+    const int D = 2 * p.n_max + 1;
+    return sizeof(cx<double>) * (size_t)p.nz * p.nz * p.nz * p.nb * p.nb * (D * 4 + 2 * D - 1);
 }
 
 cudaError_t launch_edge_correct(const PostArgs& p, const double* ups, const double* norm,
@@ -228,6 +372,47 @@ cudaError_t launch_to_gamma(const PostArgs& p, const double* gam, int projection
     if (blocks > 65535) blocks = 65535;
     if (blocks < 1) blocks = 1;
     to_gamma_kernel<<<(unsigned)blocks, 256, 0, st>>>(p, gam, projection, out);
+    return cudaGetLastError();
+}
+
+// Adjoint of to_gamma: dL/dGamma_n = sum_k dL/dGamma(phi_k) conj(R(phi_k)) e^{-i n phi_k}, with
+// R the centroid factor (projection 1) or 1. Thread per (Z-triplet, mu, b1, b2, n); overwrites.
+__global__ void to_gamma_adjoint_kernel(const PostArgs p, const double* __restrict__ gphi, int proj,
+                                        double* __restrict__ ggam)
+{
+    const int nb = p.nb, nmax = p.n_max, D = 2 * nmax + 1, np = p.n_phi;
+    const int64_t total = (int64_t)p.nz * p.nz * p.nz * 4 * D * nb * nb;
+    const cx<double>* Gp = reinterpret_cast<const cx<double>*>(gphi);
+    cx<double>* O = reinterpret_cast<cx<double>*>(ggam);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int b2 = (int)(t % nb), b1 = (int)((t / nb) % nb);
+        const int nn = (int)((t / ((int64_t)nb * nb)) % D) - nmax;
+        const int64_t zm = t / ((int64_t)nb * nb * D);  // zt * 4 + mu
+        const cx<double>* g = Gp + (((size_t)zm * nb + b1) * nb + b2) * np;
+        double sr = 0.0, si = 0.0;
+        for (int k = 0; k < np; ++k) {
+            double s, c;
+            sincospi((2.0 * k + 1.0) / np, &s, &c);
+            double sn, cn;
+            sincospi((double)nn * (2.0 * k + 1.0) / np, &sn, &cn);
+            cx<double> v = cmul(g[k], cx<double>{cn, -sn});  // e^{-i n phi_k}
+            if (proj) v = cmul(v, cconj(centroid_factor((int)(zm % 4), p.nodes[b1], p.nodes[b2], cx<double>{c, s})));
+            sr += v.x;
+            si += v.y;
+        }
+        O[t] = cx<double>{sr, si};
+    }
+}
+
+cudaError_t launch_to_gamma_adjoint(const PostArgs& p, const double* gphi, int projection, double* ggam,
+                                    cudaStream_t st)
+{
+    const int64_t total = (int64_t)p.nz * p.nz * p.nz * 4 * (2 * p.n_max + 1) * p.nb * p.nb;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    if (blocks < 1) blocks = 1;
+    to_gamma_adjoint_kernel<<<(unsigned)blocks, 256, 0, st>>>(p, gphi, projection, ggam);
     return cudaGetLastError();
 }
 
@@ -363,6 +548,69 @@ __global__ void map3_final_kernel(int jobs, int chunks, const double* __restrict
         o[6] = (-r3 + r2 + r1 - r0) / 4.0;
         o[7] = (i3 + i2 + i1 - i0) / 4.0;
     }
+}
+
+// Adjoint of the aperture measures: the correlators are c_mu = sum gcen_mu F_mu w (w = the
+// d theta1 d theta2 d phi weights) and m8 = L c (Eqs. MapTrafo8_1-8, a real linear map of the
+// real and imaginary parts). With dL/dc = L^T dL/dm8 (+ dL/dcorr), dL/dgcen_mu =
+// sum_apertures dL/dc_mu conj(F_mu) w. Thread per gcen element; overwrites.
+__device__ __forceinline__ void map3_corr_grad(const double* gm8, const double* gcorr, size_t job, double g[8])
+{
+    for (int q = 0; q < 8; ++q) g[q] = gcorr ? gcorr[job * 8 + q] : 0.0;
+    if (gm8) {
+        const double* o = gm8 + job * 8;
+        // transpose of the combination in map3_final_kernel; g = (r0, i0, r1, i1, r2, i2, r3, i3)
+        g[0] += (o[0] - o[4] - o[5] - o[6]) / 4.0;
+        g[2] += (o[0] - o[4] + o[5] + o[6]) / 4.0;
+        g[4] += (o[0] + o[4] - o[5] + o[6]) / 4.0;
+        g[6] += (o[0] + o[4] + o[5] - o[6]) / 4.0;
+        g[1] += (o[1] + o[2] + o[3] - o[7]) / 4.0;
+        g[3] += (-o[1] + o[2] + o[3] + o[7]) / 4.0;
+        g[5] += (o[1] - o[2] + o[3] + o[7]) / 4.0;
+        g[7] += (o[1] + o[2] - o[3] + o[7]) / 4.0;
+    }
+}
+
+__global__ void map3_adjoint_kernel(const PostArgs p, int n_ap, const double* __restrict__ theta,
+                                    const double* __restrict__ gcorr, const double* __restrict__ gm8,
+                                    double* __restrict__ ggcen)
+{
+    const int nb = p.nb, np = p.n_phi;
+    const int64_t npts = (int64_t)4 * nb * nb * np;
+    const int64_t total = (int64_t)p.nz * p.nz * p.nz * npts;
+    const double dphi = 2.0 * M_PI / np;
+    cx<double>* O = reinterpret_cast<cx<double>*>(ggcen);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t zt = t / npts, r = t % npts;
+        const int k = (int)(r % np);
+        const int64_t rest = r / np;
+        const int b2 = (int)(rest % nb), b1 = (int)((rest / nb) % nb), mu = (int)(rest / ((int64_t)nb * nb));
+        double s, c;
+        sincospi((2.0 * k + 1.0) / np, &s, &c);
+        const double t1 = p.nodes[b1], t2 = p.nodes[b2];
+        const double w = (p.edges[b1 + 1] - p.edges[b1]) * (p.edges[b2 + 1] - p.edges[b2]) * dphi;
+        cx<double> acc{0.0, 0.0};
+        for (int ap = 0; ap < n_ap; ++ap) {
+            double g[8];
+            map3_corr_grad(gm8, gcorr, (size_t)zt * n_ap + ap, g);
+            const double th[3] = {theta[3 * ap], theta[3 * ap + 1], theta[3 * ap + 2]};
+            const cx<double> F = aperture_filter(mu, t1, t2, cx<double>{c, s}, th);
+            acc = cadd(acc, cscale(cmul(cx<double>{g[2 * mu], g[2 * mu + 1]}, cconj(F)), w));
+        }
+        O[t] = acc;
+    }
+}
+
+cudaError_t launch_to_map3_adjoint(const PostArgs& p, int n_ap, const double* theta, const double* gcorr,
+                                   const double* gm8, double* ggcen, cudaStream_t st)
+{
+    const int64_t total = (int64_t)p.nz * p.nz * p.nz * 4 * p.nb * p.nb * p.n_phi;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    if (blocks < 1) blocks = 1;
+    map3_adjoint_kernel<<<(unsigned)blocks, 256, 0, st>>>(p, n_ap, theta, gcorr, gm8, ggcen);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_to_map3(const PostArgs& p, const double* gcen, int n_ap, const double* theta,
