@@ -57,7 +57,11 @@ typedef struct {
     int32_t precision;     /* mp3pcf_precision */
     int32_t norm_truncate; /* 1: drop N_m with |m| > n_max from the coupling matrix */
     int32_t radial_nodes;  /* 0: bin node (e_b+e_{b+1})/2, 1: sqrt(e_b e_{b+1}) */
-    int32_t reserved[5];   /* must be zero */
+    int32_t cell_occupancy;  /* tile shape of the moment kernel: target galaxies per grid cell and
+                              * redshift bin, 0 = default (4), else 1..64 (an autotuner picks it) */
+    int32_t contract_slices; /* slices of the centre axis in the tensor-core contraction, 0 = auto
+                              * (whole waves of resident CTAs), else 1..64 */
+    int32_t reserved[3];     /* must be zero */
 } mp3pcf_config;
 
 typedef struct mp3pcf_ctx mp3pcf_ctx;
@@ -155,6 +159,43 @@ mp3pcf_status mp3pcf_to_gamma(mp3pcf_ctx* ctx, const double* d_gamma_n, int32_t 
  * <Map Map Mx>, <Map Mx Mx>, <Mx Map Mx>, <Mx Mx Map>, Mx^3. Either output may be NULL. */
 mp3pcf_status mp3pcf_to_map3(mp3pcf_ctx* ctx, const double* d_gamma_cen, int64_t n_ap,
                              const double* d_theta_ap, double* d_corr, double* d_m8);
+
+/* ---- Batching form: many catalogs (mock realisations, each possibly tomographic), uneven
+ * galaxy counts, through the whole path with captured CUDA graphs. */
+
+/* One catalog in device memory (caller-owned, the layout of mp3pcf_accumulate_moments; zbin may
+ * be NULL only when n_z = 1). */
+typedef struct {
+    int64_t n;
+    const int32_t* xq;
+    const int32_t* yq;
+    const float* g1;
+    const float* g2;
+    const float* w;
+    const uint8_t* zbin;
+} mp3pcf_catalog_view;
+
+/* Fixed patch extent h_extent[4] = (x0, y0, x1, y1) in position quanta (host), or NULL to go back
+ * to measuring each catalog's extent. With a fixed extent mp3pcf_accumulate_moments makes no host
+ * round trip for the cell grid; positions outside the extent (or zbin >= n_z) set an error that
+ * mp3pcf_counts reports as EINVAL. Without a centre mask the whole path (accumulate, contract,
+ * edge_correct with h_n_singular = NULL, to_gamma, to_map3) then runs without host
+ * synchronisation and can be captured into a CUDA graph once the workspace has reached its size. */
+mp3pcf_status mp3pcf_set_extent(mp3pcf_ctx* ctx, const int64_t* h_extent);
+
+/* Runs the whole path (all centres, FP64 edge correction, centroid projection, aperture measures)
+ * for n_cats catalogs inside the extent h_extent[4] and writes d_m8 [n_cats][n_z^3][n_ap][8]
+ * (device) for the apertures d_theta_ap [n_ap][3]. The largest catalog runs first and sizes the
+ * workspace; with use_graphs != 0 every other catalog's launches are captured into a CUDA graph
+ * and replayed, one instantiated graph being updated in place (uneven counts only change kernel
+ * parameters and grid sizes). Synchronises once at the end; EINVAL if a galaxy lies outside the
+ * extent. The context's fixed extent and tracing switch are restored afterwards. */
+mp3pcf_status mp3pcf_run_batch(mp3pcf_ctx* ctx, const mp3pcf_catalog_view* h_cats, int64_t n_cats,
+                               const int64_t* h_extent, int64_t n_ap, const double* d_theta_ap, double* d_m8,
+                               int32_t use_graphs);
+
+/* CUDA-graph launches and instantiations made by mp3pcf_run_batch so far (host outputs). */
+mp3pcf_status mp3pcf_graph_stats(mp3pcf_ctx* ctx, int64_t* h_launches, int64_t* h_instantiations);
 
 /* ---- Adjoints (reverse mode), the differentiation form: dL/d(gamma_1, gamma_2, w) for a real
  * loss L of the aperture measures, by the chain to_map3 -> to_gamma -> edge_correct ->

@@ -58,10 +58,11 @@ class Estimator:
 
     def __init__(self, n_bins, theta_min, theta_max, n_max, *, n_phi=100, n_z=1,
                  quantum=2.0 ** -13, precision="fp32", norm_truncate=False,
-                 radial_nodes="arithmetic", stream=None):
+                 radial_nodes="arithmetic", cell_occupancy=0, contract_slices=0, stream=None):
         torch = _torch()
         self.cfg = native.make_config(n_bins, theta_min, theta_max, n_max, n_phi, n_z, quantum,
-                                      precision, norm_truncate, radial_nodes)
+                                      precision, norm_truncate, radial_nodes, cell_occupancy,
+                                      contract_slices)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.precision = precision
@@ -190,6 +191,48 @@ class Estimator:
         native.check(native.lib().mp3pcf_to_map3(self._ctx, _ptr(gamma_cen), n_ap, _ptr(th),
                                                  _ptr(corr), _ptr(m8)), "mp3pcf_to_map3", self._ctx)
         return corr, m8
+
+    # ------------------------------------------------------------------ batching
+    def set_extent(self, extent):
+        """Fixed patch extent (x0, y0, x1, y1) in position quanta, or None."""
+        if extent is None:
+            native.check(native.lib().mp3pcf_set_extent(self._ctx, None), "mp3pcf_set_extent", self._ctx)
+            return
+        e = (C.c_int64 * 4)(*[int(v) for v in extent])
+        native.check(native.lib().mp3pcf_set_extent(self._ctx, e), "mp3pcf_set_extent", self._ctx)
+
+    def run_batch(self, catalogs, extent, theta_ap, use_graphs=True):
+        """m8 [n_cats][n_z^3][n_ap][8] for a list of device catalogs (xq, yq, g1, g2, w[, zbin]) of
+        any sizes inside a common extent, through mp3pcf_run_batch (CUDA graphs by default)."""
+        torch = _torch()
+        th = torch.as_tensor(np.atleast_2d(np.asarray(theta_ap, dtype=np.float64)),
+                             device=self.device).contiguous()
+        views = (native.CatalogView * max(1, len(catalogs)))()
+        for i, cat in enumerate(catalogs):
+            xq, yq, g1, g2, w = cat[:5]
+            zb = cat[5] if len(cat) > 5 else None
+            n = int(xq.numel())
+            for t, dt, nm in ((xq, torch.int32, "xq"), (yq, torch.int32, "yq"), (g1, torch.float32, "g1"),
+                              (g2, torch.float32, "g2"), (w, torch.float32, "w")):
+                _need(t, dt, nm, n)
+            _need(zb, torch.uint8, "zbin", n)
+            views[i] = native.CatalogView(n, _ptr(xq), _ptr(yq), _ptr(g1), _ptr(g2), _ptr(w), _ptr(zb))
+        m8 = torch.empty((len(catalogs), self.z3, th.shape[0], 8), dtype=torch.float64, device=self.device)
+        e = (C.c_int64 * 4)(*[int(v) for v in extent])
+        native.check(native.lib().mp3pcf_run_batch(self._ctx, views, len(catalogs), e, th.shape[0], _ptr(th),
+                                                   _ptr(m8), int(bool(use_graphs))),
+                     "mp3pcf_run_batch", self._ctx)
+        return m8
+
+    def last_error(self) -> str:
+        r = native.lib().mp3pcf_last_error(self._ctx)
+        return r.decode() if r else ""
+
+    def graph_stats(self):
+        """(CUDA-graph launches, instantiations) made by run_batch so far."""
+        a, b = C.c_int64(), C.c_int64()
+        native.check(native.lib().mp3pcf_graph_stats(self._ctx, C.byref(a), C.byref(b)), "mp3pcf_graph_stats")
+        return int(a.value), int(b.value)
 
     # ------------------------------------------------------------------ adjoints
     def to_map3_adjoint(self, theta_ap, grad_m8=None, grad_corr=None):

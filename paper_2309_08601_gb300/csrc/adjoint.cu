@@ -407,12 +407,12 @@ static cudaError_t run(const AdjArgs<T>& a, int64_t n, const int* perm, const fl
         contract_adjoint_moments<T><<<g1d, 256, 0, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const size_t sm_coef = sizeof(cx<T>) * (size_t)a.nb * a.nb;
-        e = cudaFuncSetAttribute(contract_adjoint_coef<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_coef);
+        e = set_smem_attr(contract_adjoint_coef<T>, sm_coef);
         if (e != cudaSuccess) return e;
         contract_adjoint_coef<T><<<(a.n_centres + 127) / 128, 128, sm_coef, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const size_t sm_pair = sizeof(cx<T>) * (size_t)kPairWarps * a.nz * (MG + MW);
-        e = cudaFuncSetAttribute(moments_adjoint_pairs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_pair);
+        e = set_smem_attr(moments_adjoint_pairs<T>, sm_pair);
         if (e != cudaSuccess) return e;
         const int blocks = (int)std::min<int64_t>((a.n_centres + kPairWarps - 1) / kPairWarps, (int64_t)n_sm * 32);
         moments_adjoint_pairs<T><<<blocks, kPairWarps * 32, sm_pair, st>>>(a);

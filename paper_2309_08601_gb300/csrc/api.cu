@@ -7,12 +7,43 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
 
 namespace mp3 {
+
+static std::mutex g_attr_mu;
+static std::map<const void*, size_t> g_smem_set;
+static std::map<std::tuple<const void*, int, size_t>, int> g_occ;
+
+cudaError_t set_smem_attr(const void* func, size_t bytes)
+{
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    auto it = g_smem_set.find(func);
+    if (it != g_smem_set.end() && it->second >= bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) g_smem_set[func] = bytes;
+    return e;
+}
+
+cudaError_t occupancy(int* per_sm, const void* func, int threads, size_t smem)
+{
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    const auto key = std::make_tuple(func, threads, smem);
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) {
+        *per_sm = it->second;
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, func, threads, smem);
+    if (e == cudaSuccess) g_occ[key] = *per_sm;
+    return e;
+}
 
 // ------------------------------------------------------------------ device buffers
 
@@ -44,6 +75,24 @@ struct DevBuf {
 };
 
 // ------------------------------------------------------------------ a0: cell sort kernels
+
+// fixed-extent mode: every position inside [x0, x1] x [y0, y1] and zbin < nz, else bit 4 of err
+__global__ void k_validate(int64_t n, const int32_t* __restrict__ xq, const int32_t* __restrict__ yq,
+                           const uint8_t* __restrict__ zb, int nz, long long x0, long long y0, long long x1,
+                           long long y1, unsigned long long* err)
+{
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const long long x = xq[i], y = yq[i];
+        bad |= x < x0 || x > x1 || y < y0 || y > y1 || (zb && zb[i] >= nz);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, 4ULL);
+}
+
+__global__ void k_or_word(const unsigned long long* __restrict__ src, unsigned long long* dst)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst |= *src;
+}
 
 __global__ void k_bbox_init(int* bb)
 {
@@ -294,6 +343,13 @@ struct mp3pcf_ctx {
     int64_t n = 0;
     int64_t n_centres = 0;
     GridDesc grid{};
+    // fixed patch extent (fixed-point x0, y0, x1, y1): no host round trip for the cell grid
+    bool fixed_extent = false;
+    int64_t ext[4] = {0, 0, 0, 0};
+    DevBuf bups, bnorm, bgam, bgcen, berr;  // batch workspace
+    int64_t graph_launches = 0, graph_instantiations = 0;
+    cudaStream_t batch_st = nullptr;  // capturable stream of mp3pcf_run_batch (created on first use)
+    cudaEvent_t batch_ev[2] = {nullptr, nullptr};
     DevBuf d_e2q, d_edges, d_nodes;
     DevBuf bb, key, count, fill, scan_sums, scan_total, perm, pos, pay, zs;
     DevBuf cflag, crank, oflag, orank, centre_idx, crow;
@@ -373,6 +429,8 @@ static bool config_valid(const mp3pcf_config* c, std::string* why)
     if (c->precision < MP3PCF_FP64 || c->precision > MP3PCF_FP32_TF32X3) return bad("precision");
     if (c->norm_truncate != 0 && c->norm_truncate != 1) return bad("norm_truncate");
     if (c->radial_nodes != 0 && c->radial_nodes != 1) return bad("radial_nodes");
+    if (c->cell_occupancy < 0 || c->cell_occupancy > 64) return bad("cell_occupancy out of range");
+    if (c->contract_slices < 0 || c->contract_slices > 64) return bad("contract_slices out of range");
     for (int r : c->reserved)
         if (r != 0) return bad("reserved fields must be zero");
     const double t = c->theta_max / c->quantum;
@@ -455,8 +513,11 @@ mp3pcf_status mp3pcf_destroy(mp3pcf_ctx* ctx)
                       &ctx->crank, &ctx->oflag, &ctx->orank, &ctx->centre_idx, &ctx->crow,
                       &ctx->G, &ctx->W, &ctx->pairs, &ctx->partial, &ctx->singular,
                       &ctx->m3partial, &ctx->ccoef, &ctx->gG, &ctx->gW, &ctx->gv, &ctx->gw,
-                      &ctx->adjscratch};
+                      &ctx->adjscratch, &ctx->bups, &ctx->bnorm, &ctx->bgam, &ctx->bgcen, &ctx->berr};
     for (DevBuf* b : bufs) b->release();
+    if (ctx->batch_st) cudaStreamDestroy(ctx->batch_st);
+    for (cudaEvent_t ev : ctx->batch_ev)
+        if (ev) cudaEventDestroy(ev);
     for (auto& pr : ctx->ev) {
         cudaEventDestroy(pr.second.first);
         cudaEventDestroy(pr.second.second);
@@ -513,15 +574,27 @@ static mp3pcf_status accumulate_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq,
     MP3_CK(cudaMemsetAsync(ctx->pairs.p, 0, 16, st));
     if (n == 0) return MP3PCF_OK;
 
-    // ---- extent of the catalog (one host round trip)
+    // ---- extent of the catalog: given (fixed-extent mode, validated on the device), or one
+    // host round trip
     cudaEvent_t t_sort = stage_begin(ctx);
-    ctx->launches[ST_SORT] += 2;
-    k_bbox_init<<<1, 1, 0, st>>>(ctx->bb.as<int>());
-    k_bbox<<<grid1d(n, ctx->n_sm), 256, 0, st>>>(n, xq, yq, zb, nz, ctx->bb.as<int>());
-    MP3_CK(cudaGetLastError());
-    int bb[5];
-    MP3_CK(cudaMemcpyAsync(bb, ctx->bb.p, sizeof(bb), cudaMemcpyDeviceToHost, st));
-    MP3_CK(cudaStreamSynchronize(st));
+    long long bb[5];
+    if (ctx->fixed_extent) {
+        for (int i = 0; i < 4; ++i) bb[i] = ctx->ext[i];
+        bb[4] = 0;
+        ctx->launches[ST_SORT] += 1;
+        k_validate<<<grid1d(n, ctx->n_sm), 256, 0, st>>>(n, xq, yq, zb, nz, bb[0], bb[1], bb[2], bb[3],
+                                                          ctx->pairs.as<unsigned long long>() + 1);
+        MP3_CK(cudaGetLastError());
+    } else {
+        ctx->launches[ST_SORT] += 2;
+        k_bbox_init<<<1, 1, 0, st>>>(ctx->bb.as<int>());
+        k_bbox<<<grid1d(n, ctx->n_sm), 256, 0, st>>>(n, xq, yq, zb, nz, ctx->bb.as<int>());
+        MP3_CK(cudaGetLastError());
+        int hb[5];
+        MP3_CK(cudaMemcpyAsync(hb, ctx->bb.p, sizeof(hb), cudaMemcpyDeviceToHost, st));
+        MP3_CK(cudaStreamSynchronize(st));
+        for (int i = 0; i < 5; ++i) bb[i] = hb[i];
+    }
     if (bb[4]) {
         stage_end(ctx, ST_SORT, t_sort);
         return fail(ctx, MP3PCF_EINVAL, "zbin value >= n_z");
@@ -535,7 +608,8 @@ static mp3pcf_status accumulate_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq,
     // ---- cell grid: ~4 galaxies per cell and bin, and at most kMaxRows rows per annulus
     const double R = sqrt((double)ctx->e2q[nb]);
     const double area = (double)(ex + 1) * (double)(ey + 1);
-    double side = sqrt(area * 4.0 / std::max(1.0, (double)n / nz));
+    const double occ = c.cell_occupancy > 0 ? (double)c.cell_occupancy : 4.0;
+    double side = sqrt(area * occ / std::max(1.0, (double)n / nz));
     side = std::max(side, (2.0 * R + 16.0) / (kMaxRows - 4));
     side = std::max(side, sqrt(area * nz / (double)(1 << 26)));
     side = std::max(side, 1.0);
@@ -650,6 +724,7 @@ mp3pcf_status mp3pcf_counts(mp3pcf_ctx* ctx, int64_t* h_n_centres, int64_t* h_n_
     MP3_CK(cudaMemcpyAsync(p, ctx->pairs.p, 16, cudaMemcpyDeviceToHost, ctx->st));
     MP3_CK(cudaStreamSynchronize(ctx->st));
     if (h_n_pairs) *h_n_pairs = (int64_t)p[0];
+    if (p[1] & 4ULL) return fail(ctx, MP3PCF_EINVAL, "a galaxy lies outside the fixed extent or has zbin >= n_z");
     if (p[1]) return fail(ctx, MP3PCF_ETIMEOUT, "a bounded device wait in the moment or contraction kernel gave up");
     return MP3PCF_OK;
 }
@@ -692,14 +767,15 @@ mp3pcf_status mp3pcf_contract_multipoles(mp3pcf_ctx* ctx, double* d_upsilon, dou
                               0, nullptr};
         int splits = 0;
         unsigned long long* errw = ctx->pairs.as<unsigned long long>() + 1;
-        MP3_CK(launch_contract_tc(a, tf32, ctx->n_sm, nullptr, errw, &splits, true, ctx->st));
+        MP3_CK(launch_contract_tc(a, tf32, ctx->n_sm, nullptr, errw, &splits, true, c.contract_slices, ctx->st));
         MP3_CK(ctx->partial.ensure(sizeof(double) * 2 * (size_t)splits * groups * nb * nb));
         MP3_CK(ctx->ccoef.ensure(sizeof(float4) * (size_t)nc));
         a.splits = splits;
         a.partial = ctx->partial.as<double>();
         StageScope sc(ctx, ST_CONTRACT);
         ctx->launches[ST_CONTRACT] += 3;
-        MP3_CK(launch_contract_tc(a, tf32, ctx->n_sm, ctx->ccoef.as<float4>(), errw, &splits, false, ctx->st));
+        MP3_CK(launch_contract_tc(a, tf32, ctx->n_sm, ctx->ccoef.as<float4>(), errw, &splits, false,
+                                  c.contract_slices, ctx->st));
         MP3_CK(launch_contract_reduce(ctx->partial.as<double>(), splits, nz, nb, c.n_max, d_upsilon, d_norm,
                                       ctx->st));
         return MP3PCF_OK;
@@ -791,6 +867,183 @@ mp3pcf_status mp3pcf_to_map3(mp3pcf_ctx* ctx, const double* d_gamma_cen, int64_t
     ctx->launches[ST_MAP3] += 2;
     MP3_CK(launch_to_map3(post_args(ctx), d_gamma_cen, (int)n_ap, d_theta_ap,
                           ctx->m3partial.as<double>(), chunks, d_corr, d_m8, ctx->st));
+    return MP3PCF_OK;
+}
+
+// ------------------------------------------------------------------ batching
+
+mp3pcf_status mp3pcf_set_extent(mp3pcf_ctx* ctx, const int64_t* h_extent)
+{
+    if (!ctx) return MP3PCF_EINVAL;
+    ctx->err.clear();
+    if (!h_extent) {
+        ctx->fixed_extent = false;
+        return MP3PCF_OK;
+    }
+    const int64_t x0 = h_extent[0], y0 = h_extent[1], x1 = h_extent[2], y1 = h_extent[3];
+    if (x1 < x0 || y1 < y0 || x0 < INT_MIN || y0 < INT_MIN || x1 > INT_MAX || y1 > INT_MAX)
+        return fail(ctx, MP3PCF_EINVAL, "bad extent");
+    if (x1 - x0 >= (1LL << 24) || y1 - y0 >= (1LL << 24))
+        return fail(ctx, MP3PCF_EINVAL, "patch extent must be below 2^24 position quanta");
+    for (int i = 0; i < 4; ++i) ctx->ext[i] = h_extent[i];
+    ctx->fixed_extent = true;
+    return MP3PCF_OK;
+}
+
+// the whole path for one catalog of a batch into m8 (no host synchronisation)
+static mp3pcf_status batch_one(mp3pcf_ctx* ctx, const mp3pcf_catalog_view& cv, int64_t n_ap, const double* theta,
+                               double* m8)
+{
+    const mp3pcf_config& c = ctx->cfg;
+    const size_t z3 = (size_t)c.n_z * c.n_z * c.n_z, nbb = (size_t)c.n_bins * c.n_bins;
+    MP3_CK(cudaMemsetAsync(ctx->bups.p, 0, sizeof(double) * 2 * z3 * 4 * (c.n_max + 1) * nbb, ctx->st));
+    MP3_CK(cudaMemsetAsync(ctx->bnorm.p, 0, sizeof(double) * 2 * z3 * (2 * c.n_max + 1) * nbb, ctx->st));
+    mp3pcf_status s = mp3pcf_accumulate_moments(ctx, cv.n, cv.xq, cv.yq, cv.g1, cv.g2, cv.w, cv.zbin, nullptr);
+    if (s == MP3PCF_OK) s = mp3pcf_contract_multipoles(ctx, ctx->bups.as<double>(), ctx->bnorm.as<double>());
+    if (s == MP3PCF_OK)
+        s = mp3pcf_edge_correct(ctx, ctx->bups.as<double>(), ctx->bnorm.as<double>(), ctx->bgam.as<double>(), nullptr);
+    if (s == MP3PCF_OK) s = mp3pcf_to_gamma(ctx, ctx->bgam.as<double>(), 1, ctx->bgcen.as<double>());
+    if (s == MP3PCF_OK) s = mp3pcf_to_map3(ctx, ctx->bgcen.as<double>(), n_ap, theta, nullptr, m8);
+    if (s != MP3PCF_OK) return s;
+    k_or_word<<<1, 32, 0, ctx->st>>>(ctx->pairs.as<unsigned long long>() + 1, ctx->berr.as<unsigned long long>());
+    MP3_CK(cudaGetLastError());
+    return MP3PCF_OK;
+}
+
+mp3pcf_status mp3pcf_run_batch(mp3pcf_ctx* ctx, const mp3pcf_catalog_view* h_cats, int64_t n_cats,
+                               const int64_t* h_extent, int64_t n_ap, const double* d_theta_ap, double* d_m8,
+                               int32_t use_graphs)
+{
+    if (!ctx || n_cats < 0 || (n_cats > 0 && (!h_cats || !h_extent || !d_m8)) || n_ap < 1 || n_ap > 65535 ||
+        !d_theta_ap)
+        return fail(ctx, MP3PCF_EINVAL, "bad argument");
+    ctx->err.clear();
+    if (n_cats == 0) return MP3PCF_OK;
+    for (int64_t i = 0; i < n_cats; ++i) {
+        const mp3pcf_catalog_view& v = h_cats[i];
+        if (v.n < 1 || v.n > INT_MAX / 2 || !v.xq || !v.yq || !v.g1 || !v.g2 || !v.w || (ctx->cfg.n_z > 1 && !v.zbin))
+            return fail(ctx, MP3PCF_EINVAL, "bad catalog view");
+    }
+    const bool had_extent = ctx->fixed_extent;
+    int64_t old_ext[4];
+    for (int i = 0; i < 4; ++i) old_ext[i] = ctx->ext[i];
+    if (mp3pcf_status s = mp3pcf_set_extent(ctx, h_extent)) return s;
+    const bool had_timing = ctx->timing;
+    ctx->timing = false;
+    // the batch runs on a private non-blocking stream (the caller's may be the legacy default
+    // stream, which cannot be captured), ordered after the caller's stream and before its next work
+    if (!ctx->batch_st) {
+        cudaError_t ec = cudaStreamCreateWithFlags(&ctx->batch_st, cudaStreamNonBlocking);
+        for (int i = 0; ec == cudaSuccess && i < 2; ++i)
+            ec = cudaEventCreateWithFlags(&ctx->batch_ev[i], cudaEventDisableTiming);
+        if (ec != cudaSuccess) {
+            ctx->timing = had_timing;
+            ctx->fixed_extent = had_extent;
+            for (int i = 0; i < 4; ++i) ctx->ext[i] = old_ext[i];
+            return fail(ctx, MP3PCF_ECUDA, cudaGetErrorString(ec));
+        }
+    }
+    cudaStream_t user_st = ctx->st;
+    {
+        cudaError_t ec = cudaEventRecord(ctx->batch_ev[0], user_st);
+        if (ec == cudaSuccess) ec = cudaStreamWaitEvent(ctx->batch_st, ctx->batch_ev[0], 0);
+        if (ec != cudaSuccess) {
+            ctx->timing = had_timing;
+            ctx->fixed_extent = had_extent;
+            for (int i = 0; i < 4; ++i) ctx->ext[i] = old_ext[i];
+            return fail(ctx, MP3PCF_ECUDA, cudaGetErrorString(ec));
+        }
+    }
+    ctx->st = ctx->batch_st;
+    const mp3pcf_config& c = ctx->cfg;
+    const size_t z3 = (size_t)c.n_z * c.n_z * c.n_z, nbb = (size_t)c.n_bins * c.n_bins, D = 2 * c.n_max + 1;
+    const size_t out_stride = z3 * (size_t)n_ap * 8;
+    auto restore = [&](mp3pcf_status s) {
+        if (cudaEventRecord(ctx->batch_ev[1], ctx->batch_st) == cudaSuccess)
+            cudaStreamWaitEvent(user_st, ctx->batch_ev[1], 0);
+        ctx->st = user_st;
+        ctx->timing = had_timing;
+        ctx->fixed_extent = had_extent;
+        for (int i = 0; i < 4; ++i) ctx->ext[i] = old_ext[i];
+        return s;
+    };
+    cudaError_t e;
+    if ((e = ctx->bups.ensure(sizeof(double) * 2 * z3 * 4 * (c.n_max + 1) * nbb)) != cudaSuccess ||
+        (e = ctx->bnorm.ensure(sizeof(double) * 2 * z3 * D * nbb)) != cudaSuccess ||
+        (e = ctx->bgam.ensure(sizeof(double) * 2 * z3 * 4 * D * nbb)) != cudaSuccess ||
+        (e = ctx->bgcen.ensure(sizeof(double) * 2 * z3 * 4 * nbb * c.n_phi)) != cudaSuccess ||
+        (e = ctx->berr.ensure(16)) != cudaSuccess ||
+        (e = cudaMemsetAsync(ctx->berr.p, 0, 16, ctx->st)) != cudaSuccess)
+        return restore(fail(ctx, MP3PCF_ECUDA, cudaGetErrorString(e)));
+    // the largest catalog runs first, uncaptured, so that every workspace buffer is at its final
+    // size before any capture (a capture may not allocate)
+    int64_t big = 0;
+    for (int64_t i = 1; i < n_cats; ++i)
+        if (h_cats[i].n > h_cats[big].n) big = i;
+    if (mp3pcf_status s = batch_one(ctx, h_cats[big], n_ap, d_theta_ap, d_m8 + (size_t)big * out_stride))
+        return restore(s);
+    cudaGraphExec_t exec = nullptr;
+    mp3pcf_status status = MP3PCF_OK;
+    std::string capture_note;  // why a capture fell back to direct execution (first occurrence)
+    for (int64_t i = 0; i < n_cats && status == MP3PCF_OK; ++i) {
+        if (i == big) continue;
+        double* out = d_m8 + (size_t)i * out_stride;
+        if (!use_graphs) {
+            status = batch_one(ctx, h_cats[i], n_ap, d_theta_ap, out);
+            continue;
+        }
+        // capture the catalog's launches; the instantiated graph is updated in place when only
+        // kernel parameters and grid sizes change (uneven galaxy counts), else re-instantiated
+        cudaGraph_t graph = nullptr;
+        cudaError_t eb = cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal);
+        bool captured = eb == cudaSuccess;
+        mp3pcf_status s = captured ? batch_one(ctx, h_cats[i], n_ap, d_theta_ap, out) : MP3PCF_ECUDA;
+        const std::string during = s != MP3PCF_OK ? ctx->err : std::string();
+        cudaError_t ee = captured ? cudaStreamEndCapture(ctx->st, &graph) : eb;
+        if (captured && (ee != cudaSuccess || !graph)) captured = false;
+        if (!captured || s != MP3PCF_OK) {
+            if (capture_note.empty())
+                capture_note = std::string("graph capture fell back to direct launches: ") +
+                               (!during.empty() ? during : std::string(cudaGetErrorString(ee)));
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            status = batch_one(ctx, h_cats[i], n_ap, d_theta_ap, out);  // run it directly
+            continue;
+        }
+        if (exec) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(exec, graph, &info) != cudaSuccess) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(exec);
+                exec = nullptr;
+            }
+        }
+        if (!exec) {
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            if (e == cudaSuccess) ++ctx->graph_instantiations;
+        }
+        e = exec ? cudaGraphLaunch(exec, ctx->st) : cudaErrorUnknown;
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) status = fail(ctx, MP3PCF_ECUDA, cudaGetErrorString(e));
+        else ++ctx->graph_launches;
+    }
+    unsigned long long berr = 0;
+    e = cudaMemcpyAsync(&berr, ctx->berr.p, 8, cudaMemcpyDeviceToHost, ctx->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (status != MP3PCF_OK) return restore(status);
+    if (!capture_note.empty()) ctx->err = capture_note;  // not an error: the results are complete
+    if (e != cudaSuccess) return restore(fail(ctx, MP3PCF_ECUDA, cudaGetErrorString(e)));
+    if (berr & 4ULL) return restore(fail(ctx, MP3PCF_EINVAL, "a galaxy lies outside the extent or has zbin >= n_z"));
+    if (berr) return restore(fail(ctx, MP3PCF_ETIMEOUT, "a bounded device wait gave up"));
+    return restore(MP3PCF_OK);
+}
+
+mp3pcf_status mp3pcf_graph_stats(mp3pcf_ctx* ctx, int64_t* h_launches, int64_t* h_instantiations)
+{
+    if (!ctx) return MP3PCF_EINVAL;
+    if (h_launches) *h_launches = ctx->graph_launches;
+    if (h_instantiations) *h_instantiations = ctx->graph_instantiations;
     return MP3PCF_OK;
 }
 

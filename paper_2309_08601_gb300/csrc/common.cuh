@@ -119,7 +119,8 @@ cudaError_t launch_contract_f64(const ContractArgs<double>& a, cudaStream_t st);
 // number of centre slices (*splits) without launching; coef is scratch for n_centres float4;
 // err receives bit 2 if a bounded wait gave up
 cudaError_t launch_contract_tc(const ContractArgs<float>& a, bool tf32, int n_sm, float4* coef,
-                               unsigned long long* err, int* splits, bool plan_only, cudaStream_t st);
+                               unsigned long long* err, int* splits, bool plan_only, int fixed_slices,
+                               cudaStream_t st);
 cudaError_t launch_contract_reduce(const double* partial, int splits, int nz, int nb, int n_max,
                                    double* ups, double* norm, cudaStream_t st);
 
@@ -177,6 +178,23 @@ cudaError_t launch_edge_correct_adjoint(const PostArgs& p, const double* norm, c
                                         const double* ggam, double* scratch, double* gups, double* gnorm,
                                         cudaStream_t st);
 size_t edge_correct_adjoint_scratch(const PostArgs& p);
+
+// Kernel attributes and occupancy, set and queried once per (kernel, size) per process: neither
+// call is permitted while a stream is being captured into a CUDA graph, so every launch goes
+// through these caches (the first, uncaptured, call fills them).
+cudaError_t set_smem_attr(const void* func, size_t bytes);
+cudaError_t occupancy(int* per_sm, const void* func, int threads, size_t smem);
+
+template <typename F>
+inline cudaError_t set_smem_attr(F* func, size_t bytes)
+{
+    return set_smem_attr(reinterpret_cast<const void*>(func), bytes);
+}
+template <typename F>
+inline cudaError_t occupancy(int* per_sm, F* func, int threads, size_t smem)
+{
+    return occupancy(per_sm, reinterpret_cast<const void*>(func), threads, smem);
+}
 
 __host__ __device__ inline int groups_per_zt(int n_max) { return 4 * (n_max + 1) + 2 * n_max + 1; }
 

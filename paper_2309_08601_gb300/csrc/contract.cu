@@ -154,11 +154,11 @@ static cudaError_t launch_contract_t(const ContractArgs<T>& a, cudaStream_t st)
     const size_t smem = sizeof(cx<T>) * 2 * kTile * a.nb;
     cudaError_t e = cudaSuccess;
     if (nbb <= kThreads)
-        e = cudaFuncSetAttribute(contract_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = set_smem_attr(contract_kernel<T, 1>, smem);
     else if (nbb <= 4 * kThreads)
-        e = cudaFuncSetAttribute(contract_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = set_smem_attr(contract_kernel<T, 4>, smem);
     else
-        e = cudaFuncSetAttribute(contract_kernel<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = set_smem_attr(contract_kernel<T, 16>, smem);
     if (e != cudaSuccess) return e;
     if (nbb <= kThreads)
         contract_kernel<T, 1><<<grid, kThreads, smem, st>>>(a);

@@ -145,6 +145,7 @@ struct TcArgs {
     int npad;     // MMA N: gt * 2 nb rounded up to 16
     int nbp;      // bins padded to even (the moment rows)
     int ta, tw;   // tiles per component of Upsilon (n_max + 1 orders) and of N (2 n_max + 1 orders)
+    int fixed_slices;  // > 0: this many centre slices instead of the automatic choice
     unsigned long long* err;
 };
 
@@ -657,14 +658,15 @@ static cudaError_t launch_tc(TcArgs a, float4* coef, int n_sm, int* splits_out, 
     const ContractArgs<float>& c = a.c;
     const size_t smem = smem_bytes<SP>(SP::KT, c.nb, a.nbp, a.gt);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_smem_attr(contract_tc_kernel<SP>, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, contract_tc_kernel<SP>, kThreads, smem);
+    e = occupancy(&per_sm, contract_tc_kernel<SP>, kThreads, smem);
     if (e != cudaSuccess) return e;
     per_sm = std::max(1, std::min(per_sm, 512 / (2 * kTmemCols)));
     const int tiles = c.nz * c.nz * c.nz * (4 * a.ta + a.tw);
-    const int slices = pick_slices(tiles, per_sm * n_sm, c.n_centres, SP::KT);
+    const int slices = a.fixed_slices > 0 ? (int)std::min<int64_t>(a.fixed_slices, std::max<int64_t>(1, c.n_centres))
+                                          : pick_slices(tiles, per_sm * n_sm, c.n_centres, SP::KT);
     *splits_out = slices;
     if (plan_only) return cudaSuccess;
     if (slices != c.splits) return cudaErrorInvalidValue;  // partial buffer sized for another plan
@@ -696,9 +698,11 @@ static cudaError_t launch_tc(TcArgs a, float4* coef, int n_sm, int* splits_out, 
 }  // namespace tc
 
 cudaError_t launch_contract_tc(const ContractArgs<float>& c, bool tf32, int n_sm, float4* coef,
-                               unsigned long long* err, int* splits, bool plan_only, cudaStream_t st)
+                               unsigned long long* err, int* splits, bool plan_only, int fixed_slices,
+                               cudaStream_t st)
 {
     tc::TcArgs a;
+    a.fixed_slices = fixed_slices;
     a.c = c;
     a.groups = c.nz * c.nz * c.nz * groups_per_zt(c.n_max);
     a.gt = std::min(tc::kMaxGroups, tc::kM / (2 * c.nb));

@@ -446,11 +446,10 @@ cudaError_t launch_moments_nmax(const MomentArgs<T>& a, int n_sm, cudaStream_t s
 {
     using PL = MomPlan<T, NMAX>;
     const size_t smem = sizeof(MomSmemOf<T, NMAX>) + sizeof(T) * PL::P * PL::NAP;
-    cudaError_t e = cudaFuncSetAttribute(moments_kernel<T, NMAX>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_smem_attr(moments_kernel<T, NMAX>, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, moments_kernel<T, NMAX>, PL::NT, smem);
+    e = occupancy(&per_sm, moments_kernel<T, NMAX>, PL::NT, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     long long grid = (long long)n_sm * per_sm;

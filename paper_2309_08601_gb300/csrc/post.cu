@@ -281,8 +281,7 @@ cudaError_t launch_edge_correct_adjoint(const PostArgs& p, const double* norm, c
 {
     const int D = 2 * p.n_max + 1;
     const size_t smem = sizeof(cx<double>) * ((size_t)D * D + (size_t)D * 8);
-    cudaError_t e = cudaFuncSetAttribute(edge_correct_adjoint_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_smem_attr(edge_correct_adjoint_kernel, smem);
     if (e != cudaSuccess) return e;
     const int systems = p.nz * p.nz * p.nz * p.nb * p.nb;
     edge_correct_adjoint_kernel<<<systems, 256, smem, st>>>(p, norm, gam, ggam, scratch);
@@ -305,8 +304,7 @@ cudaError_t launch_edge_correct(const PostArgs& p, const double* ups, const doub
 {
     const int D = 2 * p.n_max + 1;
     const size_t smem = sizeof(cx<double>) * ((size_t)D * D + (size_t)D * 4);
-    cudaError_t e = cudaFuncSetAttribute(edge_correct_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_smem_attr(edge_correct_kernel, smem);
     if (e != cudaSuccess) return e;
     const int systems = p.nz * p.nz * p.nz * p.nb * p.nb;
     edge_correct_kernel<<<systems, 256, smem, st>>>(p, ups, norm, gam, nsing);

@@ -21,7 +21,8 @@ class Config(C.Structure):
     _fields_ = [("n_bins", C.c_int32), ("theta_min", C.c_double), ("theta_max", C.c_double),
                 ("n_max", C.c_int32), ("n_phi", C.c_int32), ("n_z", C.c_int32),
                 ("quantum", C.c_double), ("precision", C.c_int32), ("norm_truncate", C.c_int32),
-                ("radial_nodes", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("radial_nodes", C.c_int32), ("cell_occupancy", C.c_int32),
+                ("contract_slices", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 P = C.c_void_p
@@ -47,7 +48,15 @@ SIGNATURES = {
     "mp3pcf_to_gamma_adjoint": ([P, I32, P, P], C.c_int),
     "mp3pcf_edge_correct_adjoint": ([P, P, P, P, P, P], C.c_int),
     "mp3pcf_moments_adjoint": ([P, P, P, I64, P, P, P, P, P, P], C.c_int),
+    "mp3pcf_set_extent": ([P, P], C.c_int),
+    "mp3pcf_run_batch": ([P, P, I64, P, I64, P, P, I32], C.c_int),
+    "mp3pcf_graph_stats": ([P, P, P], C.c_int),
 }
+
+
+class CatalogView(C.Structure):
+    _fields_ = [("n", C.c_int64), ("xq", C.c_void_p), ("yq", C.c_void_p), ("g1", C.c_void_p),
+                ("g2", C.c_void_p), ("w", C.c_void_p), ("zbin", C.c_void_p)]
 
 _lib = None
 
@@ -89,9 +98,10 @@ def check(status: int, where: str, ctx=None, ok=(OK,)):
 
 
 def make_config(n_bins, theta_min, theta_max, n_max, n_phi=100, n_z=1, quantum=2.0 ** -13,
-                precision="fp32", norm_truncate=False, radial_nodes="arithmetic") -> Config:
+                precision="fp32", norm_truncate=False, radial_nodes="arithmetic", cell_occupancy=0,
+                contract_slices=0) -> Config:
     return Config(int(n_bins), float(theta_min), float(theta_max), int(n_max), int(n_phi), int(n_z),
                   float(quantum), PRECISIONS[precision] if isinstance(precision, str) else int(precision),
                   int(bool(norm_truncate)),
                   {"arithmetic": 0, "geometric": 1}[radial_nodes] if isinstance(radial_nodes, str)
-                  else int(radial_nodes), (C.c_int32 * 5)())
+                  else int(radial_nodes), int(cell_occupancy), int(contract_slices), (C.c_int32 * 3)())

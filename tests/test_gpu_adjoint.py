@@ -110,7 +110,7 @@ def _euler(api, cat, setup, theta, precision, c):
         L.backward()
     eg = (g1.detach().double() * g1.grad.double() + g2.detach().double() * g2.grad.double())
     ew = w.detach().double() * w.grad.double()
-    return float(L), float(eg.sum()), float(eg.abs().sum()), float(ew.sum()), float(ew.abs().sum())
+    return float(L.detach()), float(eg.sum()), float(eg.abs().sum()), float(ew.sum()), float(ew.abs().sum())
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-6), ("fp32", 1e-4)])
