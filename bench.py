@@ -45,7 +45,11 @@ HBM_PEAK_GBS = _measured_hbm_gbs()
 # workload: ncu capture at 50 000 galaxies (profiles/moments_kernel_lognormal_50k.md) scaled to
 # 200 000 centres (the traffic is the G/W write, proportional to the number of centres).
 # Set to None whenever the kernel changes until it is captured again.
-MOMENTS_TRAFFIC_BYTES = None  # the kernel's output layout changed since the last capture
+MOMENTS_TRAFFIC_BYTES = 4 * (86.325248e6 + 1012.321e6)
+# DRAM bytes per launch of the tensor-core contraction (BF16x3) at lognormal_200k: ncu capture
+# at 50 000 galaxies (profiles/contract_tc_bf16x3_lognormal_50k.md) scaled to 200 000 centres
+# (the traffic is the moment stream, proportional to the centres). None whenever it changes.
+CONTRACT_TRAFFIC_BYTES = 4 * (1.033375e9 + 8.868096e6)
 
 
 def flops_per_pair(n_max: int) -> int:
@@ -307,7 +311,10 @@ def run_gpu(args):
     roofline_contract = {"bound": "hbm", "kernel": "contract (%s)" % args.precision,
                          "achieved": k2_bytes / (k2_ms / 1e3) / 1e9, "peak": HBM_PEAK_GBS, "unit": "GB/s",
                          "frac": k2_bytes / (k2_ms / 1e3) / 1e9 / HBM_PEAK_GBS, "bytes_per_launch": k2_bytes,
-                         "launch_ms": k2_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+                         "launch_ms": k2_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                         "traffic": (CONTRACT_TRAFFIC_BYTES if (args.workload == "lognormal_200k" and not args.n
+                                                                and args.precision == "bf16x3") else None),
+                         "traffic_note": "ncu DRAM read+write, capture at 50 000 galaxies scaled by centres"}
 
     # ---- end to end through the public API with host buffers
     host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
