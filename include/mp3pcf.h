@@ -160,6 +160,15 @@ mp3pcf_status mp3pcf_to_gamma(mp3pcf_ctx* ctx, const double* d_gamma_n, int32_t 
 mp3pcf_status mp3pcf_to_map3(mp3pcf_ctx* ctx, const double* d_gamma_cen, int64_t n_ap,
                              const double* d_theta_ap, double* d_corr, double* d_m8);
 
+/* ---- Failure injection, for tests of failure detection (host side only; nothing faults or
+ * traps the GPU). MP3PCF_INJECT_WAIT_TIMEOUT: the tensor-core contraction issues no TMA copies,
+ * so its bounded mbarrier waits (about a second each) run out; every role aborts, frees its
+ * tensor memory and returns, the partial sums are zero, and the next mp3pcf_counts returns
+ * ETIMEOUT; the context stays usable. MP3PCF_INJECT_ALLOC_FAILURE: mp3pcf_accumulate_moments
+ * fails with ENOMEM before touching the workspace. on = 0 switches an injection off. */
+enum { MP3PCF_INJECT_WAIT_TIMEOUT = 1, MP3PCF_INJECT_ALLOC_FAILURE = 2 };
+mp3pcf_status mp3pcf_inject(mp3pcf_ctx* ctx, int32_t what, int32_t on);
+
 /* ---- Batching form: many catalogs (mock realisations, each possibly tomographic), uneven
  * galaxy counts, through the whole path with captured CUDA graphs. */
 

@@ -349,6 +349,8 @@ struct mp3pcf_ctx {
     DevBuf bups, bnorm, bgam, bgcen, berr;  // batch workspace
     int64_t graph_launches = 0, graph_instantiations = 0;
     cudaStream_t batch_st = nullptr;  // capturable stream of mp3pcf_run_batch (created on first use)
+    // fault injection on the host side (tests of failure detection): see mp3pcf_inject
+    bool inject_wait_timeout = false, inject_alloc_failure = false;
     cudaEvent_t batch_ev[2] = {nullptr, nullptr};
     DevBuf d_e2q, d_edges, d_nodes;
     DevBuf bb, key, count, fill, scan_sums, scan_total, perm, pos, pay, zs;
@@ -573,6 +575,7 @@ static mp3pcf_status accumulate_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq,
     ctx->n_centres = 0;
     MP3_CK(cudaMemsetAsync(ctx->pairs.p, 0, 16, st));
     if (n == 0) return MP3PCF_OK;
+    if (ctx->inject_alloc_failure) return fail(ctx, MP3PCF_ENOMEM, "injected allocation failure");
 
     // ---- extent of the catalog: given (fixed-extent mode, validated on the device), or one
     // host round trip
@@ -767,7 +770,7 @@ mp3pcf_status mp3pcf_contract_multipoles(mp3pcf_ctx* ctx, double* d_upsilon, dou
                               0, nullptr};
         int splits = 0;
         unsigned long long* errw = ctx->pairs.as<unsigned long long>() + 1;
-        MP3_CK(launch_contract_tc(a, tf32, ctx->n_sm, nullptr, errw, &splits, true, c.contract_slices, ctx->st));
+        MP3_CK(launch_contract_tc(a, tf32, ctx->n_sm, nullptr, errw, &splits, true, c.contract_slices, 0, ctx->st));
         MP3_CK(ctx->partial.ensure(sizeof(double) * 2 * (size_t)splits * groups * nb * nb));
         MP3_CK(ctx->ccoef.ensure(sizeof(float4) * (size_t)nc));
         a.splits = splits;
@@ -775,7 +778,7 @@ mp3pcf_status mp3pcf_contract_multipoles(mp3pcf_ctx* ctx, double* d_upsilon, dou
         StageScope sc(ctx, ST_CONTRACT);
         ctx->launches[ST_CONTRACT] += 3;
         MP3_CK(launch_contract_tc(a, tf32, ctx->n_sm, ctx->ccoef.as<float4>(), errw, &splits, false,
-                                  c.contract_slices, ctx->st));
+                                  c.contract_slices, ctx->inject_wait_timeout ? 1 : 0, ctx->st));
         MP3_CK(launch_contract_reduce(ctx->partial.as<double>(), splits, nz, nb, c.n_max, d_upsilon, d_norm,
                                       ctx->st));
         return MP3PCF_OK;
@@ -868,6 +871,19 @@ mp3pcf_status mp3pcf_to_map3(mp3pcf_ctx* ctx, const double* d_gamma_cen, int64_t
     MP3_CK(launch_to_map3(post_args(ctx), d_gamma_cen, (int)n_ap, d_theta_ap,
                           ctx->m3partial.as<double>(), chunks, d_corr, d_m8, ctx->st));
     return MP3PCF_OK;
+}
+
+// ------------------------------------------------------------------ failure injection
+
+mp3pcf_status mp3pcf_inject(mp3pcf_ctx* ctx, int32_t what, int32_t on)
+{
+    if (!ctx) return MP3PCF_EINVAL;
+    ctx->err.clear();
+    switch (what) {
+        case MP3PCF_INJECT_WAIT_TIMEOUT: ctx->inject_wait_timeout = on != 0; return MP3PCF_OK;
+        case MP3PCF_INJECT_ALLOC_FAILURE: ctx->inject_alloc_failure = on != 0; return MP3PCF_OK;
+        default: return fail(ctx, MP3PCF_EINVAL, "unknown injection");
+    }
 }
 
 // ------------------------------------------------------------------ batching

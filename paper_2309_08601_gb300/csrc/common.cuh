@@ -120,7 +120,7 @@ cudaError_t launch_contract_f64(const ContractArgs<double>& a, cudaStream_t st);
 // err receives bit 2 if a bounded wait gave up
 cudaError_t launch_contract_tc(const ContractArgs<float>& a, bool tf32, int n_sm, float4* coef,
                                unsigned long long* err, int* splits, bool plan_only, int fixed_slices,
-                               cudaStream_t st);
+                               int skip_copies, cudaStream_t st);
 cudaError_t launch_contract_reduce(const double* partial, int splits, int nz, int nb, int n_max,
                                    double* ups, double* norm, cudaStream_t st);
 

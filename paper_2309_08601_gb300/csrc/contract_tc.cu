@@ -146,6 +146,7 @@ struct TcArgs {
     int nbp;      // bins padded to even (the moment rows)
     int ta, tw;   // tiles per component of Upsilon (n_max + 1 orders) and of N (2 n_max + 1 orders)
     int fixed_slices;  // > 0: this many centre slices instead of the automatic choice
+    int skip_copies;   // test hook: issue no TMA copies, so every wait on them runs out
     unsigned long long* err;
 };
 
@@ -364,6 +365,7 @@ __global__ void __launch_bounds__(kThreads, 2) contract_tc_kernel(const __grid_c
                 const int slot = s % kRaw;
                 if (s >= kRaw && !wait_or_abort(smem_u32(&rawempty[slot]), ((s / kRaw) - 1) & 1, &abort_flag, a.err))
                     break;
+                if (a.skip_copies) continue;
                 const uint32_t dst = smem_u32(raw + slot * R.slot_bytes);
                 const uint32_t bar = smem_u32(&rawfull[slot]);
                 const int cb = c0 + s * KT;
@@ -483,6 +485,9 @@ __global__ void __launch_bounds__(kThreads, 2) contract_tc_kernel(const __grid_c
             if (good) good = wait_or_abort(smem_u32(&rawfull[slot]), (s / kRaw) & 1, &abort_flag, a.err);
             if (good && s >= kStages)
                 good = wait_or_abort(smem_u32(&opempty[st]), ((s / kStages) - 1) & 1, &abort_flag, a.err);
+            // one outcome per warp: a lane that saw the abort flag before the barrier completed
+            // must not leave its warp split at the __syncwarp below
+            good = __all_sync(0xffffffffu, good);
             if (good) {
                 // ---- convert: L = coef X (conj), R = Y (conj), split hi/lo into the operand layout
                 const float2* rx = reinterpret_cast<const float2*>(raw + slot * R.slot_bytes);
@@ -699,10 +704,11 @@ static cudaError_t launch_tc(TcArgs a, float4* coef, int n_sm, int* splits_out, 
 
 cudaError_t launch_contract_tc(const ContractArgs<float>& c, bool tf32, int n_sm, float4* coef,
                                unsigned long long* err, int* splits, bool plan_only, int fixed_slices,
-                               cudaStream_t st)
+                               int skip_copies, cudaStream_t st)
 {
     tc::TcArgs a;
     a.fixed_slices = fixed_slices;
+    a.skip_copies = skip_copies;
     a.c = c;
     a.groups = c.nz * c.nz * c.nz * groups_per_zt(c.n_max);
     a.gt = std::min(tc::kMaxGroups, tc::kM / (2 * c.nb));

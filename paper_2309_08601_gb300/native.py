@@ -51,7 +51,9 @@ SIGNATURES = {
     "mp3pcf_set_extent": ([P, P], C.c_int),
     "mp3pcf_run_batch": ([P, P, I64, P, I64, P, P, I32], C.c_int),
     "mp3pcf_graph_stats": ([P, P, P], C.c_int),
+    "mp3pcf_inject": ([P, I32, I32], C.c_int),
 }
+INJECT_WAIT_TIMEOUT, INJECT_ALLOC_FAILURE = 1, 2
 
 
 class CatalogView(C.Structure):
