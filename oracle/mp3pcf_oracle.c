@@ -54,6 +54,7 @@ typedef struct {
     double quantum; /* arcmin per fixed-point unit */
     int32_t norm_truncate; /* 1: N_m = 0 for |m| > n_max in the coupling matrix */
     int32_t radial_nodes;  /* 0: arithmetic midpoint, 1: geometric midpoint */
+    int32_t exclude_degenerate; /* 1: triplets with j = k are left out of Upsilon and N */
 } orc_cfg;
 
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_ESINGULAR = 5 };
@@ -317,6 +318,58 @@ int orc_contract(const orc_cfg* c, const float* g1, const float* g2, const float
  *      Upsilon_{3,n}(j,i), N_{-n}(i,j) = N_n(j,i), with Z2 <-> Z3). ---- */
 
 /* Gaussian elimination with partial pivoting, in place; A is D x D row-major, B is D x R. */
+/* With exclude_degenerate: subtracts from Upsilon and N (as produced by orc_contract) the
+ * contributions of the triplets with j = k. In the sums of Eqs. Upsilon0_Derivation, Upsilon1-3
+ * and 3PCF_Normalization such a triplet pairs a neighbour k with itself, so it only occurs for
+ * b1 = b2 (and Z2 = Z3 = Z of k); each term is the product of the two moment terms of that one
+ * neighbour, evaluated here straight from those products for every n. */
+int orc_degenerate_correction(const orc_cfg* c, int64_t n, const int32_t* xq, const int32_t* yq,
+                              const float* g1, const float* g2, const float* w, const uint8_t* zbin,
+                              int64_t n_centres, const int64_t* centres, double* ups_io, double* norm_io)
+{
+    if (!cfg_ok(c) || n < 0 || n_centres < 0) return ORC_EINVAL;
+    if (!c->exclude_degenerate) return ORC_OK;
+    const int nb = c->n_bins, nmax = c->n_max, nz = c->n_z, NN = nmax + 1, NW = 2 * nmax + 1;
+    int64_t* e2q = (int64_t*)malloc(sizeof(int64_t) * (nb + 1));
+    orc_edges(c, NULL, e2q);
+    cplx* ups = (cplx*)ups_io;
+    cplx* norm = (cplx*)norm_io;
+    for (int64_t ci = 0; ci < n_centres; ++ci) {
+        const int64_t i = centres[ci];
+        const int z1 = zbin ? zbin[i] : 0;
+        const double wi = (double)w[i];
+        const cplx vi = wi * ((double)g1[i] + I * (double)g2[i]);
+        for (int64_t k = 0; k < n; ++k) {
+            const int64_t dx = (int64_t)xq[k] - xq[i], dy = (int64_t)yq[k] - yq[i];
+            const int b = bin_of(dx * dx + dy * dy, e2q, nb);
+            if (b < 0) continue;
+            const double phi = atan2((double)dy, (double)dx);
+            const int zk = zbin ? zbin[k] : 0;
+            const int zt = (z1 * nz + zk) * nz + zk;
+            const double wk = (double)w[k];
+            const cplx vk = wk * ((double)g1[k] + I * (double)g2[k]);
+            for (int m = 0; m <= nmax; ++m) {
+                /* the same neighbour as the X and the Y moment term of each component */
+                const cplx x0 = vk * cexp(I * (m - 3) * phi), y0 = vk * cexp(I * (-m - 3) * phi);
+                const cplx x1 = vk * cexp(I * (m - 1) * phi), y1 = vk * cexp(I * (-m - 1) * phi);
+                const cplx x2 = conj(vk * cexp(I * (-m - 1) * phi)), y2 = vk * cexp(I * (-m - 3) * phi);
+                const cplx x3 = vk * cexp(I * (m - 3) * phi), y3 = conj(vk * cexp(I * (m - 1) * phi));
+                const size_t at = (size_t)b * nb + b;
+                ups[(((size_t)zt * 4 + 0) * NN + m) * nb * nb + at] -= -vi * x0 * y0;
+                ups[(((size_t)zt * 4 + 1) * NN + m) * nb * nb + at] -= -conj(vi) * x1 * y1;
+                ups[(((size_t)zt * 4 + 2) * NN + m) * nb * nb + at] -= -vi * x2 * y2;
+                ups[(((size_t)zt * 4 + 3) * NN + m) * nb * nb + at] -= -vi * x3 * y3;
+            }
+            for (int m = 0; m < NW; ++m) {
+                const cplx wx = wk * cexp(I * m * phi);
+                norm[((size_t)zt * NW + m) * nb * nb + (size_t)b * nb + b] -= wi * wx * conj(wx);
+            }
+        }
+    }
+    free(e2q);
+    return ORC_OK;
+}
+
 static int solve_lu(int D, int R, cplx* A, cplx* B)
 {
     for (int k = 0; k < D; ++k) {
@@ -711,6 +764,7 @@ int orc_brute(const orc_cfg* c, int64_t n, const int32_t* xq, const int32_t* yq,
                 const cplx gj = (double)g1[j] + I * (double)g2[j];
                 for (int bb = 0; bb < cnt; ++bb) {
                     const int k = nbr[bb], b2 = nbb[bb];
+                    if (c->exclude_degenerate && k == j) continue;
                     const double dxk = (double)((int64_t)xq[k] - xq[i]), dyk = (double)((int64_t)yq[k] - yq[i]);
                     const double phi2 = atan2(dyk, dxk);
                     const int z3 = zbin ? zbin[k] : 0;

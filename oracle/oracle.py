@@ -31,7 +31,7 @@ class OrcCfg(C.Structure):
     _fields_ = [("n_bins", C.c_int32), ("theta_min", C.c_double), ("theta_max", C.c_double),
                 ("n_max", C.c_int32), ("n_phi", C.c_int32), ("n_z", C.c_int32),
                 ("quantum", C.c_double), ("norm_truncate", C.c_int32),
-                ("radial_nodes", C.c_int32)]
+                ("radial_nodes", C.c_int32), ("exclude_degenerate", C.c_int32)]
 
 
 @dataclass
@@ -46,10 +46,12 @@ class Setup:
     quantum: float = 2.0 ** -13
     norm_truncate: int = 0
     radial_nodes: int = 0
+    exclude_degenerate: int = 0
 
     def c(self) -> OrcCfg:
         return OrcCfg(self.n_bins, self.theta_min, self.theta_max, self.n_max, self.n_phi,
-                      self.n_z, self.quantum, self.norm_truncate, self.radial_nodes)
+                      self.n_z, self.quantum, self.norm_truncate, self.radial_nodes,
+                      self.exclude_degenerate)
 
 
 _lib = None
@@ -66,6 +68,7 @@ def lib():
             "orc_moments": [P, I64, P, P, P, P, P, P, I64, P, P, P],
             "orc_count_pairs": [P, I64, P, P, I64, P, P],
             "orc_contract": [P, P, P, P, P, I64, P, P, P, P, P],
+            "orc_degenerate_correction": [P, I64, P, P, P, P, P, P, I64, P, P, P],
             "orc_edge_correct": [P, P, P, P, P],
             "orc_to_gamma": [P, P, C.c_int32, P],
             "orc_to_map3": [P, P, I64, P, P, P],
@@ -156,6 +159,18 @@ def contract(s: Setup, cat, G, W, centres: Optional[np.ndarray] = None, ups=None
     cfg = s.c()
     _check(lib().orc_contract(C.byref(cfg), _p(g1), _p(g2), _p(w), _p(zb), centres.shape[0],
                               _p(centres), _p(G), _p(W), _p(ups), _p(norm)))
+    return ups, norm
+
+
+def degenerate_correction(s: Setup, cat, ups, norm, centres: Optional[np.ndarray] = None):
+    """With s.exclude_degenerate, removes the j = k triplets from (ups, norm) in place."""
+    xq, yq, g1, g2, w, zb = _cat(cat)
+    if centres is None:
+        centres = np.arange(cat.n, dtype=np.int64)
+    centres = _c(centres, np.int64)
+    cfg = s.c()
+    _check(lib().orc_degenerate_correction(C.byref(cfg), cat.n, _p(xq), _p(yq), _p(g1), _p(g2), _p(w),
+                                           _p(zb), centres.shape[0], _p(centres), _p(ups), _p(norm)))
     return ups, norm
 
 
@@ -258,6 +273,8 @@ def pipeline(s: Setup, cat, theta_ap, centres: Optional[np.ndarray] = None) -> R
     """The whole path on the oracle: moments, multipoles, edge correction, Gamma, Map^3."""
     G, W = moments(s, cat, centres)
     ups, norm = contract(s, cat, G, W, centres)
+    if s.exclude_degenerate:
+        degenerate_correction(s, cat, ups, norm, centres)
     gam, ns = edge_correct(s, ups, norm)
     gx = to_gamma(s, gam, 0)
     gc = to_gamma(s, gam, 1)
@@ -266,5 +283,5 @@ def pipeline(s: Setup, cat, theta_ap, centres: Optional[np.ndarray] = None) -> R
 
 
 __all__ = ["Setup", "build_oracle", "edges", "moments", "count_pairs", "contract",
-           "edge_correct", "to_gamma", "to_map3", "filter_F", "cen_factor", "combine8", "brute",
+           "edge_correct", "degenerate_correction", "to_gamma", "to_map3", "filter_F", "cen_factor", "combine8", "brute",
            "pipeline", "num_threads", "Result", "Brute"]

@@ -105,6 +105,38 @@ def test_tomographic_moments_equal_triplet_sums(orc):
     assert rel_err(ups.sum(axis=0), u1[0]) < 1e-12 and rel_err(norm.sum(axis=0), n1[0]) < 1e-12
 
 
+@pytest.mark.parametrize("n_z", [1, 2])
+def test_excluding_degenerate_triplets_equals_triplet_sums_without_j_eq_k(orc, n_z):
+    """exclude_degenerate (j = k left out): the moment route with the degenerate correction
+    equals the brute-force triplet sums that skip j = k; the removed part sits only on b1 = b2
+    and Z2 = Z3."""
+    rng = np.random.default_rng(17 + n_z)
+    n = 90
+    xy = rng.uniform(0, 16, (n, 2))
+    g = rng.normal(0, 0.3, n) + 1j * rng.normal(0, 0.3, n)
+    z = rng.integers(0, n_z, n) if n_z > 1 else None
+    cat = hand_catalog(xy, g, rng.uniform(0.5, 1.5, n), z)
+    kw = dict(n_bins=4, theta_min=0.8, theta_max=8.0, n_max=5, n_z=n_z)
+    s_in, s_ex = orc.Setup(**kw), orc.Setup(**kw, exclude_degenerate=1)
+    b = orc.brute(s_ex, cat)
+    G, W = orc.moments(s_ex, cat)
+    ups, norm = orc.contract(s_ex, cat, G, W)
+    u_in, n_in = ups.copy(), norm.copy()
+    orc.degenerate_correction(s_ex, cat, ups, norm)
+    assert rel_err(ups, b.ups_n) < 1e-12 and rel_err(norm, b.norm_n) < 1e-12
+    d_u, d_n = u_in - ups, n_in - norm
+    mask = np.zeros((n_z ** 3, 4, 4), bool)  # (zt, b1, b2) where j = k can occur
+    for zt in range(n_z ** 3):
+        if (zt // n_z) % n_z == zt % n_z:
+            mask[zt, np.arange(4), np.arange(4)] = True
+    assert np.abs(d_u[~mask[:, None, None].repeat(4, 1).repeat(6, 2)]).max() == 0
+    assert np.abs(d_n[~mask[:, None].repeat(11, 1)]).max() == 0
+    assert np.abs(d_n).max() > 0
+    # the default (include) equals the plain brute force
+    bi = orc.brute(s_in, cat)
+    assert rel_err(u_in, bi.ups_n) < 1e-12
+
+
 # ------------------------------------------------------ P2: exact invariants of the estimator
 
 @pytest.fixture(scope="module")
