@@ -61,7 +61,10 @@ typedef struct {
                               * redshift bin, 0 = default (4), else 1..64 (an autotuner picks it) */
     int32_t contract_slices; /* slices of the centre axis in the tensor-core contraction, 0 = auto
                               * (whole waves of resident CTAs), else 1..64 */
-    int32_t reserved[3];     /* must be zero */
+    int32_t exclude_degenerate; /* 1: leave the triplets with j = k (one neighbour in both legs, so
+                                 * b1 = b2 and Z2 = Z3) out of Upsilon and N; 0 (default): the
+                                 * paper's sums over all (i, j, k) */
+    int32_t reserved[2];     /* must be zero */
 } mp3pcf_config;
 
 typedef struct mp3pcf_ctx mp3pcf_ctx;
@@ -120,7 +123,10 @@ mp3pcf_status mp3pcf_copy_moments(mp3pcf_ctx* ctx, void* d_G, void* d_W);
  * summed over the centres of the last accumulate call and ADDED to d_upsilon
  * [n_z^3][4][n_max+1][n_bins][n_bins] (n = 0..n_max) and d_norm [n_z^3][2 n_max+1][n_bins][n_bins]
  * (n = 0..2 n_max), complex double. Adding lets callers sum centre chunks or patches
- * (App. B, Eq. PatchGamma).
+ * (App. B, Eq. PatchGamma). With exclude_degenerate the j = k triplets of these centres are
+ * removed: for b1 = b2 and Z2 = Z3, Upsilon_0 += sum_i v_i sum_k v_k^2 e^{-6i phi_ik},
+ * Upsilon_1 += sum_i v_i^* sum_k v_k^2 e^{-2i phi}, Upsilon_2,3 += sum_i v_i sum_k |v_k|^2
+ * e^{-2i phi} and N -= sum_i w_i sum_k w_k^2 (v = w gamma), for every order.
  * MP3PCF_FP64 and MP3PCF_FP32 sum on the CUDA cores (tile sums in the moment precision, added in
  * FP64). MP3PCF_FP32_BF16X3 / MP3PCF_FP32_TF32X3 run each group as real GEMMs on the tcgen05
  * tensor cores: every FP32 operand x = hi + lo (hi, lo in BF16 resp. TF32), products
@@ -239,7 +245,8 @@ mp3pcf_status mp3pcf_edge_correct_adjoint(mp3pcf_ctx* ctx, const double* d_norm,
  * LAST accumulate call (the context still holds its sorted copy and moments): ADDS dL/dgamma_1,
  * dL/dgamma_2 and dL/dw per galaxy, in the caller's order, to d_grad_g1, d_grad_g2, d_grad_w
  * (float [n]; any may be NULL) given dL/dUpsilon and dL/dN. n and d_g1, d_g2, d_w must be the
- * catalog of that call (EINVAL if n differs). Arithmetic in the forward moment precision; the
+ * catalog of that call (EINVAL if n differs; EUNSUPPORTED with exclude_degenerate). Arithmetic in
+ * the forward moment precision; the
  * scatter to neighbours uses atomics, so the result is not bit-reproducible. */
 mp3pcf_status mp3pcf_moments_adjoint(mp3pcf_ctx* ctx, const double* d_grad_upsilon, const double* d_grad_norm,
                                      int64_t n, const float* d_g1, const float* d_g2, const float* d_w,

@@ -278,6 +278,58 @@ __device__ __forceinline__ cx<double> unit_dir<double>(long long dx, long long d
 
 constexpr int kPairWarps = 4;
 
+// Calls f(k, dx, dy) on the calling lane for every galaxy k of redshift bin z whose squared
+// separation r2 from the centre (px, py) lies in [r2lo, r2hi); the warp walks, row by row of the
+// cell grid, the one or two runs of cells that meet the annulus (cells wholly inside the inner
+// radius are skipped), one candidate per lane. Must be called by the whole warp.
+template <typename F>
+__device__ __forceinline__ void for_each_in_annulus(const GridDesc& g, const int32_t* __restrict__ cell_start,
+                                                    const int2* __restrict__ pos, long long px, long long py,
+                                                    long long r2lo, long long r2hi, int z, int lane, F&& f)
+{
+    const long long R = isqrt_floor(r2hi - 1);
+    const long long ya = max(0LL, fdiv(py - R - g.y0, g.side));
+    const long long yb = min((long long)g.ncy - 1, fdiv(py + R - g.y0, g.side));
+    for (long long yy = ya; yy <= yb; ++yy) {
+        const long long ylo = g.y0 + yy * g.side, yhi = ylo + g.side - 1;
+        const long long dymin = max(0LL, max(ylo - py, py - yhi));
+        const long long dymax = max(llabs(ylo - py), llabs(yhi - py));
+        if (dymin * dymin > r2hi - 1) continue;
+        const long long dxo = isqrt_floor(r2hi - 1 - dymin * dymin);
+        long long ca = fdiv(px - dxo - g.x0, g.side), cb = fdiv(px + dxo - g.x0, g.side);
+        if (cb < 0 || ca > g.ncx - 1) continue;
+        ca = max(ca, 0LL);
+        cb = min(cb, (long long)g.ncx - 1);
+        long long cl = cb + 1, cr = cb;
+        if (r2lo - 1 - dymax * dymax >= 0) {
+            const long long hx = isqrt_floor(r2lo - 1 - dymax * dymax);
+            cl = -fdiv(-(px - hx - g.x0), g.side);      // first cell starting at >= px - hx
+            cr = fdiv(px + hx - g.x0 + 1, g.side) - 1;  // last cell ending at <= px + hx
+        }
+        long long segs[2][2];
+        int nseg = 0;
+        if (cl <= cr && cl <= cb && cr >= ca) {
+            if (ca <= cl - 1) { segs[nseg][0] = ca; segs[nseg][1] = cl - 1; ++nseg; }
+            if (cr + 1 <= cb) { segs[nseg][0] = cr + 1; segs[nseg][1] = cb; ++nseg; }
+        } else {
+            segs[0][0] = ca;
+            segs[0][1] = cb;
+            nseg = 1;
+        }
+        const size_t key0 = (size_t)z * g.ncells + (size_t)yy * g.ncx;
+        for (int sgi = 0; sgi < nseg; ++sgi) {
+            const int k0 = cell_start[key0 + segs[sgi][0]];
+            const int k1 = cell_start[key0 + segs[sgi][1] + 1];
+            for (int k = k0 + lane; k < k1; k += 32) {
+                const int2 qk = pos[k];
+                const long long dx = (long long)qk.x - px, dy = (long long)qk.y - py;
+                const long long r2 = dx * dx + dy * dy;
+                if (r2 >= r2lo && r2 < r2hi) f(k, dx, dy);
+            }
+        }
+    }
+}
+
 // warp per centre (grid-stride); per bin the warp stages the centre's adjoint moments of every Z
 // in shared memory and walks the annulus
 template <typename T>
@@ -289,11 +341,9 @@ __global__ void __launch_bounds__(kPairWarps * 32) moments_adjoint_pairs(const A
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     cx<T>* co = reinterpret_cast<cx<T>*>(smem_raw) + (size_t)warp * nz * (MG + MW);  // [z][MG + MW]
     const size_t plane = (size_t)a.n_centres * nz * nbp;
-    const GridDesc g = a.g;
     for (int c = blockIdx.x * kPairWarps + warp; c < a.n_centres; c += gridDim.x * kPairWarps) {
         const int d = a.centre_idx[c];
         const int2 p = a.pos[d];
-        const long long px = p.x, py = p.y;
         for (int b = 0; b < nb; ++b) {
             __syncwarp();
             for (int i = lane; i < nz * (MG + MW); i += 32) {
@@ -302,75 +352,35 @@ __global__ void __launch_bounds__(kPairWarps * 32) moments_adjoint_pairs(const A
                                 : a.gW[(size_t)(qq - MG) * plane + ((size_t)c * nz + z) * nbp + b];
             }
             __syncwarp();
-            const long long r2lo = a.e2q[b], r2hi = a.e2q[b + 1];  // in bin: r2lo <= r2 < r2hi
-            const long long R = isqrt_floor(r2hi - 1);
-            const long long ya = max(0LL, fdiv(py - R - g.y0, g.side));
-            const long long yb = min((long long)g.ncy - 1, fdiv(py + R - g.y0, g.side));
-            for (long long yy = ya; yy <= yb; ++yy) {
-                const long long ylo = g.y0 + yy * g.side, yhi = ylo + g.side - 1;
-                const long long dymin = max(0LL, max(ylo - py, py - yhi));
-                const long long dymax = max(llabs(ylo - py), llabs(yhi - py));
-                if (dymin * dymin > r2hi - 1) continue;
-                const long long dxo = isqrt_floor(r2hi - 1 - dymin * dymin);
-                long long ca = fdiv(px - dxo - g.x0, g.side), cb = fdiv(px + dxo - g.x0, g.side);
-                if (cb < 0 || ca > g.ncx - 1) continue;
-                ca = max(ca, 0LL);
-                cb = min(cb, (long long)g.ncx - 1);
-                // cells wholly inside the inner radius (every point at r^2 < r2lo) are skipped
-                long long cl = cb + 1, cr = cb;
-                if (r2lo - 1 - dymax * dymax >= 0) {
-                    const long long hx = isqrt_floor(r2lo - 1 - dymax * dymax);
-                    cl = -fdiv(-(px - hx - g.x0), g.side);        // first cell starting at >= px - hx
-                    cr = fdiv(px + hx - g.x0 + 1, g.side) - 1;    // last cell ending at <= px + hx
-                }
-                long long segs[2][2];
-                int nseg = 0;
-                if (cl <= cr && cl <= cb && cr >= ca) {
-                    if (ca <= cl - 1) { segs[nseg][0] = ca; segs[nseg][1] = cl - 1; ++nseg; }
-                    if (cr + 1 <= cb) { segs[nseg][0] = cr + 1; segs[nseg][1] = cb; ++nseg; }
-                } else {
-                    segs[0][0] = ca;
-                    segs[0][1] = cb;
-                    nseg = 1;
-                }
-                for (int z = 0; z < nz; ++z) {
-                    const cx<T>* gg = co + (size_t)z * (MG + MW);
-                    const cx<T>* gw = gg + MG;
-                    for (int sgi = 0; sgi < nseg; ++sgi) {
-                        const size_t key0 = (size_t)z * g.ncells + (size_t)yy * g.ncx;
-                        const int k0 = a.cell_start[key0 + segs[sgi][0]];
-                        const int k1 = a.cell_start[key0 + segs[sgi][1] + 1];
-                        for (int k = k0 + lane; k < k1; k += 32) {
-                            const int2 qk = a.pos[k];
-                            const long long dx = (long long)qk.x - px, dy = (long long)qk.y - py;
-                            const long long r2 = dx * dx + dy * dy;
-                            if (r2 < r2lo || r2 >= r2hi) continue;
-                            const cx<T> zz = unit_dir<T>(dx, dy);
-                            const cx<T> u{zz.x, -zz.y};
-                            // m >= 0 part of sum_m gG_m u^m (Horner in u)
-                            cx<T> P{T(0), T(0)};
-                            for (int mm = nmax - 1; mm >= 0; --mm) {
-                                P = cmul(P, u);
-                                P = cadd(P, gg[o + mm]);
-                            }
-                            // m < 0 part: sum_{j >= 1} gG_{-j} z^j (Horner in z)
-                            cx<T> Q{T(0), T(0)};
-                            for (int j = nmax + 3; j >= 1; --j) {
-                                Q = cadd(Q, gg[o - j]);
-                                Q = cmul(Q, zz);
-                            }
-                            // W: sum_m gW_m u^m
-                            cx<T> Rw{T(0), T(0)};
-                            for (int mm = 2 * nmax; mm >= 0; --mm) {
-                                Rw = cmul(Rw, u);
-                                Rw = cadd(Rw, gw[mm]);
-                            }
-                            atomic_add_t<T>(&a.gv[2 * (size_t)k], P.x + Q.x);
-                            atomic_add_t<T>(&a.gv[2 * (size_t)k + 1], P.y + Q.y);
-                            atomic_add_t<T>(&a.gw[k], Rw.x);
-                        }
+            for (int z = 0; z < nz; ++z) {
+                const cx<T>* gg = co + (size_t)z * (MG + MW);
+                const cx<T>* gw = gg + MG;
+                for_each_in_annulus(a.g, a.cell_start, a.pos, p.x, p.y, a.e2q[b], a.e2q[b + 1], z, lane,
+                                    [&](int k, long long dx, long long dy) {
+                    const cx<T> zz = unit_dir<T>(dx, dy);
+                    const cx<T> u{zz.x, -zz.y};
+                    // m >= 0 part of sum_m gG_m u^m (Horner in u)
+                    cx<T> P{T(0), T(0)};
+                    for (int mm = nmax - 1; mm >= 0; --mm) {
+                        P = cmul(P, u);
+                        P = cadd(P, gg[o + mm]);
                     }
-                }
+                    // m < 0 part: sum_{j >= 1} gG_{-j} z^j (Horner in z)
+                    cx<T> Q{T(0), T(0)};
+                    for (int j = nmax + 3; j >= 1; --j) {
+                        Q = cadd(Q, gg[o - j]);
+                        Q = cmul(Q, zz);
+                    }
+                    // W: sum_m gW_m u^m
+                    cx<T> Rw{T(0), T(0)};
+                    for (int mm = 2 * nmax; mm >= 0; --mm) {
+                        Rw = cmul(Rw, u);
+                        Rw = cadd(Rw, gw[mm]);
+                    }
+                    atomic_add_t<T>(&a.gv[2 * (size_t)k], P.x + Q.x);
+                    atomic_add_t<T>(&a.gv[2 * (size_t)k + 1], P.y + Q.y);
+                    atomic_add_t<T>(&a.gw[k], Rw.x);
+                });
             }
         }
     }
@@ -423,6 +433,119 @@ static cudaError_t run(const AdjArgs<T>& a, int64_t n, const int* perm, const fl
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ exclude_degenerate
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Per (centre, z, bin) the sums over neighbours k of redshift bin z in the bin that the j = k
+// triplets contribute (u = e^{-i phi}, v = w gamma): D6 = sum v^2 u^6, D2 = sum v^2 u^2,
+// E2 = sum |v|^2 u^2, F = sum w^2, written as 4 complex values (F in the real part).
+template <typename T>
+__global__ void __launch_bounds__(kPairWarps * 32) degenerate_moments(const AdjArgs<T> a, cx<T>* __restrict__ out)
+{
+    const int nb = a.nb, nz = a.nz;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c = blockIdx.x * kPairWarps + warp; c < a.n_centres; c += gridDim.x * kPairWarps) {
+        const int2 p = a.pos[a.centre_idx[c]];
+        for (int b = 0; b < nb; ++b)
+            for (int z = 0; z < nz; ++z) {
+                T s[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+                for_each_in_annulus(a.g, a.cell_start, a.pos, p.x, p.y, a.e2q[b], a.e2q[b + 1], z, lane,
+                                    [&](int k, long long dx, long long dy) {
+                    const cx<T> zz = unit_dir<T>(dx, dy);
+                    const cx<T> u{zz.x, -zz.y};
+                    const cx<T> u2 = cmul(u, u), u6 = cmul(cmul(u2, u2), u2);
+                    const Pay<T> pk = a.pay[k];
+                    const cx<T> v{pk.a, pk.b};
+                    const cx<T> v2 = cmul(v, v);
+                    const T vv = pk.a * pk.a + pk.b * pk.b;
+                    const cx<T> d6 = cmul(v2, u6), d2 = cmul(v2, u2);
+                    s[0] += d6.x;
+                    s[1] += d6.y;
+                    s[2] += d2.x;
+                    s[3] += d2.y;
+                    s[4] += vv * u2.x;
+                    s[5] += vv * u2.y;
+                    s[6] += pk.w * pk.w;
+                });
+                for (int i = 0; i < 7; ++i) s[i] = warp_sum(s[i]);
+                if (lane == 0) {
+                    cx<T>* o = out + (((size_t)c * nz + z) * nb + b) * 4;
+                    o[0] = cx<T>{s[0], s[1]};
+                    o[1] = cx<T>{s[2], s[3]};
+                    o[2] = cx<T>{s[4], s[5]};
+                    o[3] = cx<T>{s[6], T(0)};
+                }
+            }
+    }
+}
+
+// Block per (z1, z, bin): S0 = sum_i v_i D6, S1 = sum_i conj(v_i) D2, S2 = sum_i v_i E2,
+// SN = sum_i w_i F over the centres of redshift bin z1 (FP64, fixed order), then for the triplet
+// (z1, z, z) and b1 = b2 = bin, every order: Upsilon_0 += S0, Upsilon_1 += S1, Upsilon_2,3 += S2,
+// N -= SN (the j = k terms of the paper's sums, removed).
+template <typename T>
+__global__ void __launch_bounds__(256) degenerate_correct(const AdjArgs<T> a, const cx<T>* __restrict__ dm,
+                                                         double* __restrict__ ups, double* __restrict__ norm)
+{
+    const int nb = a.nb, nz = a.nz, nmax = a.n_max, NN = nmax + 1, NW = 2 * nmax + 1;
+    const int b = blockIdx.x % nb, z = (blockIdx.x / nb) % nz, z1 = blockIdx.x / (nb * nz);
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int c = threadIdx.x; c < a.n_centres; c += blockDim.x) {
+        const int d = a.centre_idx[c];
+        if ((a.zs ? (int)a.zs[d] : 0) != z1) continue;
+        const Pay<T> pv = a.pay[d];
+        const cx<double> v{(double)pv.a, (double)pv.b};
+        const cx<T>* m = dm + (((size_t)c * nz + z) * nb + b) * 4;
+        const cx<double> d6{(double)m[0].x, (double)m[0].y}, d2{(double)m[1].x, (double)m[1].y};
+        const cx<double> e2{(double)m[2].x, (double)m[2].y};
+        const cx<double> t0 = cmul(v, d6), t1 = cmul(cconj(v), d2), t2 = cmul(v, e2);
+        s[0] += t0.x; s[1] += t0.y; s[2] += t1.x; s[3] += t1.y; s[4] += t2.x; s[5] += t2.y;
+        s[6] += (double)pv.w * (double)m[3].x;
+    }
+    __shared__ double red[7][256];
+    for (int i = 0; i < 7; ++i) red[i][threadIdx.x] = s[i];
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int i = 0; i < 7; ++i) red[i][threadIdx.x] += red[i][threadIdx.x + h];
+        __syncthreads();
+    }
+    const int zt = (z1 * nz + z) * nz + z;
+    const size_t bb = (size_t)b * nb + b, nbb = (size_t)nb * nb;
+    cx<double>* U = reinterpret_cast<cx<double>*>(ups);
+    cx<double>* N = reinterpret_cast<cx<double>*>(norm);
+    for (int n = threadIdx.x; n < NN; n += blockDim.x) {
+        const cx<double> S0{red[0][0], red[1][0]}, S1{red[2][0], red[3][0]}, S2{red[4][0], red[5][0]};
+        U[(((size_t)zt * 4 + 0) * NN + n) * nbb + bb] = cadd(U[(((size_t)zt * 4 + 0) * NN + n) * nbb + bb], S0);
+        U[(((size_t)zt * 4 + 1) * NN + n) * nbb + bb] = cadd(U[(((size_t)zt * 4 + 1) * NN + n) * nbb + bb], S1);
+        U[(((size_t)zt * 4 + 2) * NN + n) * nbb + bb] = cadd(U[(((size_t)zt * 4 + 2) * NN + n) * nbb + bb], S2);
+        U[(((size_t)zt * 4 + 3) * NN + n) * nbb + bb] = cadd(U[(((size_t)zt * 4 + 3) * NN + n) * nbb + bb], S2);
+    }
+    for (int m = threadIdx.x; m < NW; m += blockDim.x) {
+        cx<double>& e = N[((size_t)zt * NW + m) * nbb + bb];
+        e.x -= red[6][0];
+    }
+}
+
+template <typename T>
+static cudaError_t run_degenerate(const AdjArgs<T>& a, cx<T>* scratch, double* ups, double* norm, int n_sm,
+                                  cudaStream_t st)
+{
+    if (a.n_centres <= 0) return cudaSuccess;
+    const int blocks = (int)std::min<int64_t>((a.n_centres + kPairWarps - 1) / kPairWarps, (int64_t)n_sm * 32);
+    degenerate_moments<T><<<blocks, kPairWarps * 32, 0, st>>>(a, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    degenerate_correct<T><<<a.nz * a.nz * a.nb, 256, 0, st>>>(a, scratch, ups, norm);
+    return cudaGetLastError();
+}
+
 }  // namespace adj
 
 cudaError_t launch_moments_adjoint_f32(const AdjArgs<float>& a, int64_t n, const int* perm, const float* g1,
@@ -437,6 +560,22 @@ cudaError_t launch_moments_adjoint_f64(const AdjArgs<double>& a, int64_t n, cons
                                        int n_sm, cudaStream_t st)
 {
     return adj::run<double>(a, n, perm, g1, g2, w, dg1, dg2, dw, n_sm, st);
+}
+
+}  // namespace mp3
+
+namespace mp3 {
+
+cudaError_t launch_degenerate_f32(const AdjArgs<float>& a, void* scratch, double* ups, double* norm, int n_sm,
+                                  cudaStream_t st)
+{
+    return adj::run_degenerate<float>(a, reinterpret_cast<cx<float>*>(scratch), ups, norm, n_sm, st);
+}
+
+cudaError_t launch_degenerate_f64(const AdjArgs<double>& a, void* scratch, double* ups, double* norm, int n_sm,
+                                  cudaStream_t st)
+{
+    return adj::run_degenerate<double>(a, reinterpret_cast<cx<double>*>(scratch), ups, norm, n_sm, st);
 }
 
 }  // namespace mp3

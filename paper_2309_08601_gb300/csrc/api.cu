@@ -357,6 +357,7 @@ struct mp3pcf_ctx {
     DevBuf cflag, crank, oflag, orank, centre_idx, crow;
     DevBuf G, W, pairs, partial, singular, m3partial, ccoef;
     DevBuf gG, gW, gv, gw, adjscratch;  // adjoint workspace
+    DevBuf degen;                       // exclude_degenerate sums per (centre, z, bin)
     // tracing: per-stage event pairs and kernel-launch counts
     bool timing = false;
     int64_t launches[6] = {0, 0, 0, 0, 0, 0};
@@ -433,6 +434,7 @@ static bool config_valid(const mp3pcf_config* c, std::string* why)
     if (c->radial_nodes != 0 && c->radial_nodes != 1) return bad("radial_nodes");
     if (c->cell_occupancy < 0 || c->cell_occupancy > 64) return bad("cell_occupancy out of range");
     if (c->contract_slices < 0 || c->contract_slices > 64) return bad("contract_slices out of range");
+    if (c->exclude_degenerate != 0 && c->exclude_degenerate != 1) return bad("exclude_degenerate");
     for (int r : c->reserved)
         if (r != 0) return bad("reserved fields must be zero");
     const double t = c->theta_max / c->quantum;
@@ -452,6 +454,9 @@ static void host_edges(const mp3pcf_config* c, std::vector<double>& e, std::vect
         e2[b] = (long long)ceil(t * t);
     }
 }
+
+template <typename T>
+static mp3pcf_status degenerate_t(mp3pcf_ctx* ctx, double* ups, double* norm);
 
 extern "C" {
 
@@ -515,7 +520,7 @@ mp3pcf_status mp3pcf_destroy(mp3pcf_ctx* ctx)
                       &ctx->crank, &ctx->oflag, &ctx->orank, &ctx->centre_idx, &ctx->crow,
                       &ctx->G, &ctx->W, &ctx->pairs, &ctx->partial, &ctx->singular,
                       &ctx->m3partial, &ctx->ccoef, &ctx->gG, &ctx->gW, &ctx->gv, &ctx->gw,
-                      &ctx->adjscratch, &ctx->bups, &ctx->bnorm, &ctx->bgam, &ctx->bgcen, &ctx->berr};
+                      &ctx->adjscratch, &ctx->degen, &ctx->bups, &ctx->bnorm, &ctx->bgam, &ctx->bgcen, &ctx->berr};
     for (DevBuf* b : bufs) b->release();
     if (ctx->batch_st) cudaStreamDestroy(ctx->batch_st);
     for (cudaEvent_t ev : ctx->batch_ev)
@@ -781,6 +786,7 @@ mp3pcf_status mp3pcf_contract_multipoles(mp3pcf_ctx* ctx, double* d_upsilon, dou
                                   c.contract_slices, ctx->inject_wait_timeout ? 1 : 0, ctx->st));
         MP3_CK(launch_contract_reduce(ctx->partial.as<double>(), splits, nz, nb, c.n_max, d_upsilon, d_norm,
                                       ctx->st));
+        if (c.exclude_degenerate) return degenerate_t<float>(ctx, d_upsilon, d_norm);
         return MP3PCF_OK;
     }
     int splits = (int)std::min<int64_t>(64, std::max<int64_t>(1, (int64_t)ctx->n_sm * 8 / groups));
@@ -804,6 +810,8 @@ mp3pcf_status mp3pcf_contract_multipoles(mp3pcf_ctx* ctx, double* d_upsilon, dou
     }
     MP3_CK(e);
     MP3_CK(launch_contract_reduce(ctx->partial.as<double>(), splits, nz, nb, c.n_max, d_upsilon, d_norm, ctx->st));
+    if (c.exclude_degenerate)
+        return ctx->fp64 ? degenerate_t<double>(ctx, d_upsilon, d_norm) : degenerate_t<float>(ctx, d_upsilon, d_norm);
     return MP3PCF_OK;
 }
 
@@ -1115,6 +1123,42 @@ mp3pcf_status mp3pcf_edge_correct_adjoint(mp3pcf_ctx* ctx, const double* d_norm,
 
 }  // extern "C"
 
+// the catalog state of the last accumulate call as AdjArgs (gradient buffers left null)
+template <typename T>
+static AdjArgs<T> catalog_args(mp3pcf_ctx* ctx)
+{
+    const mp3pcf_config& c = ctx->cfg;
+    AdjArgs<T> a{};
+    a.n_centres = (int32_t)ctx->n_centres;
+    a.nz = c.n_z;
+    a.nb = c.n_bins;
+    a.n_max = c.n_max;
+    a.centre_idx = ctx->centre_idx.as<int>();
+    a.pos = ctx->pos.as<int2>();
+    a.pay = ctx->pay.as<Pay<T>>();
+    a.zs = c.n_z > 1 ? ctx->zs.as<uint8_t>() : nullptr;
+    a.cell_start = ctx->count.as<int>();
+    a.g = ctx->grid;
+    a.e2q = ctx->d_e2q.as<long long>();
+    a.G = ctx->G.as<cx<T>>();
+    a.W = ctx->W.as<cx<T>>();
+    return a;
+}
+
+template <typename T>
+static mp3pcf_status degenerate_t(mp3pcf_ctx* ctx, double* ups, double* norm)
+{
+    const mp3pcf_config& c = ctx->cfg;
+    MP3_CK(ctx->degen.ensure(sizeof(cx<T>) * 4 * (size_t)ctx->n_centres * c.n_z * c.n_bins));
+    ctx->launches[ST_CONTRACT] += 2;
+    const AdjArgs<T> a = catalog_args<T>(ctx);
+    if constexpr (sizeof(T) == 8)
+        MP3_CK(launch_degenerate_f64(a, ctx->degen.p, ups, norm, ctx->n_sm, ctx->st));
+    else
+        MP3_CK(launch_degenerate_f32(a, ctx->degen.p, ups, norm, ctx->n_sm, ctx->st));
+    return MP3PCF_OK;
+}
+
 template <typename T>
 static mp3pcf_status moments_adjoint_t(mp3pcf_ctx* ctx, const double* gups, const double* gnorm, const float* g1,
                                        const float* g2, const float* w, float* dg1, float* dg2, float* dw)
@@ -1168,6 +1212,8 @@ mp3pcf_status mp3pcf_moments_adjoint(mp3pcf_ctx* ctx, const double* d_grad_upsil
     if (!ctx || !d_grad_upsilon || !d_grad_norm) return fail(ctx, MP3PCF_EINVAL, "null argument");
     ctx->err.clear();
     if (n != ctx->n) return fail(ctx, MP3PCF_EINVAL, "n differs from the last accumulate call");
+    if (ctx->cfg.exclude_degenerate)
+        return fail(ctx, MP3PCF_EUNSUPPORTED, "the adjoint does not cover exclude_degenerate");
     if (n == 0) return MP3PCF_OK;
     if (!d_g1 || !d_g2 || !d_w) return fail(ctx, MP3PCF_EINVAL, "null catalog pointer");
     if (ctx->fp64) return moments_adjoint_t<double>(ctx, d_grad_upsilon, d_grad_norm, d_g1, d_g2, d_w, d_grad_g1,

@@ -169,6 +169,13 @@ cudaError_t launch_moments_adjoint_f64(const AdjArgs<double>& a, int64_t n, cons
                                        const float* g2, const float* w, float* dg1, float* dg2, float* dw,
                                        int n_sm, cudaStream_t st);
 
+// exclude_degenerate: sums of the j = k triplets per (centre, z, bin) into scratch
+// (4 complex values each) and their removal from (ups, norm); AdjArgs carries the catalog state
+cudaError_t launch_degenerate_f32(const AdjArgs<float>& a, void* scratch, double* ups, double* norm, int n_sm,
+                                  cudaStream_t st);
+cudaError_t launch_degenerate_f64(const AdjArgs<double>& a, void* scratch, double* ups, double* norm, int n_sm,
+                                  cudaStream_t st);
+
 // adjoints of the FP64 stages (overwrite their outputs)
 cudaError_t launch_to_map3_adjoint(const PostArgs& p, int n_ap, const double* theta, const double* gcorr,
                                    const double* gm8, double* ggcen, cudaStream_t st);
