@@ -13,6 +13,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace mp3 {
@@ -393,12 +395,28 @@ static void stage_end(mp3pcf_ctx* ctx, int stage, cudaEvent_t b)
 }
 
 // records the end event of a stage when it goes out of scope
+// NVTX ranges (visible to nsys / ncu range filters; free without a tool): one per stage call and
+// one around each public entry point that spans stages
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+static const char* const kStageNames[6] = {"mp3pcf sort", "mp3pcf moments", "mp3pcf contract",
+                                           "mp3pcf edge_correct", "mp3pcf to_gamma", "mp3pcf to_map3"};
+
 struct StageScope {
     mp3pcf_ctx* ctx;
     int stage;
     cudaEvent_t b;
-    StageScope(mp3pcf_ctx* c, int s) : ctx(c), stage(s), b(stage_begin(c)) {}
-    ~StageScope() { stage_end(ctx, stage, b); }
+    StageScope(mp3pcf_ctx* c, int s) : ctx(c), stage(s), b(stage_begin(c)) { nvtxRangePushA(kStageNames[s]); }
+    ~StageScope()
+    {
+        stage_end(ctx, stage, b);
+        nvtxRangePop();
+    }
 };
 
 static mp3pcf_status fail(mp3pcf_ctx* c, mp3pcf_status s, const std::string& msg)
@@ -584,6 +602,7 @@ static mp3pcf_status accumulate_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq,
 
     // ---- extent of the catalog: given (fixed-extent mode, validated on the device), or one
     // host round trip
+    NvtxRange nvtx_acc("mp3pcf accumulate_moments");
     cudaEvent_t t_sort = stage_begin(ctx);
     long long bb[5];
     if (ctx->fixed_extent) {
@@ -938,6 +957,7 @@ mp3pcf_status mp3pcf_run_batch(mp3pcf_ctx* ctx, const mp3pcf_catalog_view* h_cat
                                const int64_t* h_extent, int64_t n_ap, const double* d_theta_ap, double* d_m8,
                                int32_t use_graphs)
 {
+    NvtxRange nvtx_range("mp3pcf run_batch");
     if (!ctx || n_cats < 0 || (n_cats > 0 && (!h_cats || !h_extent || !d_m8)) || n_ap < 1 || n_ap > 65535 ||
         !d_theta_ap)
         return fail(ctx, MP3PCF_EINVAL, "bad argument");
@@ -1209,6 +1229,7 @@ mp3pcf_status mp3pcf_moments_adjoint(mp3pcf_ctx* ctx, const double* d_grad_upsil
                                      int64_t n, const float* d_g1, const float* d_g2, const float* d_w,
                                      float* d_grad_g1, float* d_grad_g2, float* d_grad_w)
 {
+    NvtxRange nvtx_range("mp3pcf moments_adjoint");
     if (!ctx || !d_grad_upsilon || !d_grad_norm) return fail(ctx, MP3PCF_EINVAL, "null argument");
     ctx->err.clear();
     if (n != ctx->n) return fail(ctx, MP3PCF_EINVAL, "n differs from the last accumulate call");
