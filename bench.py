@@ -45,7 +45,7 @@ HBM_PEAK_GBS = _measured_hbm_gbs()
 # workload: ncu capture at 50 000 galaxies (profiles/moments_kernel_lognormal_50k.md) scaled to
 # 200 000 centres (the traffic is the G/W write, proportional to the number of centres).
 # Set to None whenever the kernel changes until it is captured again.
-MOMENTS_TRAFFIC_BYTES = 4 * (86.325248e6 + 1012.321e6)
+MOMENTS_TRAFFIC_BYTES = 4 * (124.231168e6 + 1053.384e6)
 # DRAM bytes per launch of the tensor-core contraction (BF16x3) at lognormal_200k: ncu capture
 # at 50 000 galaxies (profiles/contract_tc_bf16x3_lognormal_50k.md) scaled to 200 000 centres
 # (the traffic is the moment stream, proportional to the centres). None whenever it changes.
@@ -53,9 +53,18 @@ CONTRACT_TRAFFIC_BYTES = 4 * (1.033375e9 + 8.868096e6)
 
 
 def flops_per_pair(n_max: int) -> int:
-    """Algorithmic FP32 flops of stage (a) per neighbour pair in this formulation: unit vector
-    (6), powers z^2..z^{2n_max} (6 per complex product), A_m and B_m for m <= n_max+3 (4 each,
-    real x complex multiply-add), W_m for m <= 2 n_max (4 each)."""
+    """Algorithmic FP32 flops of stage (a) per neighbour pair, counted for the plain form of
+    Eq. Gn_disc and the W_n of Eq. 3PCF_Normalization: geometry (15), the powers z^1..z^{2 n_max}
+    (2 n_max complex products, 6 flops each), 2 n_max + 3 complex multiply-adds into G (8 each)
+    and 2 n_max + 1 real x complex multiply-adds into W (4 each): 36 n_max + 43."""
+    return 15 + 6 * 2 * n_max + 8 * (2 * n_max + 3) + 4 * (2 * n_max + 1)
+
+
+def kernel_flops_per_pair(n_max: int) -> int:
+    """The flops the moment kernel's own formulation needs per pair (fewer than the plain form:
+    with real weights, G_m and G_-m come from the same two real sums A_m = sum w g1 z^m and
+    B_m = sum w g2 z^m): unit vector (6), powers z^2..z^{2 n_max} (6 each), A_m and B_m for
+    m <= n_max + 3 (4 each), W_m for m <= 2 n_max (4 each)."""
     return 6 + 6 * (2 * n_max - 1) + 8 * (n_max + 4) + 4 * (2 * n_max + 1)
 
 
@@ -300,6 +309,9 @@ def run_gpu(args):
                                                        and args.precision != "fp64") else None)),
                 "traffic_note": "ncu DRAM read+write, capture at 50 000 galaxies scaled by centres",
                 "flops_per_pair": fpp, "pairs_per_launch": pairs,
+                "kernel_flops_per_pair": kernel_flops_per_pair(p["n_max"]),
+                "frac_kernel_flops": kernel_flops_per_pair(p["n_max"]) * pairs / (k1_ms / 1e3) / 1e12
+                / FP32_PEAK_TFLOPS,
                 "launch_ms": k1_ms, "peak_source": PEAK_NOTE}
     launches = sum(v[1] for v in stages.values())
     # ---- stage (b): HBM-bound; algorithmic bytes = every moment row read once (complex, moment

@@ -14,7 +14,7 @@ namespace mp3 {
 constexpr int kMaxBins = 64;   // radial bins supported by the device kernels
 constexpr int kMaxNmax = 50;   // largest multipole order
 constexpr int kMaxNz = 8;      // tomographic bins
-constexpr int kMaxRows = 512;  // cell rows an annulus may span (host picks the cell side)
+constexpr int kMaxRows = 480;  // cell rows an annulus may span (host picks the cell side)
 
 // ------------------------------------------------------------------ complex helpers
 

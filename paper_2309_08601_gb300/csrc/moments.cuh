@@ -27,11 +27,13 @@
 #include "common.cuh"
 
 // Tiling parameters (compile-time; the defaults are the tuned values).
+// At n_max <= 30 (four warps) the FP32 kernel then holds 4 CTAs per SM: 128 registers per
+// thread and 57 KB of shared memory per CTA (with kMaxRows = 480).
 #ifndef MP3_MOM_SCR_F32
-#define MP3_MOM_SCR_F32 192  // candidates per warp and round (FP32)
+#define MP3_MOM_SCR_F32 160  // candidates per warp and round (FP32)
 #endif
 #ifndef MP3_MOM_MINB_F32
-#define MP3_MOM_MINB_F32 3  // CTAs per SM the FP32 register budget is sized for
+#define MP3_MOM_MINB_F32 4  // CTAs per SM the FP32 register budget is sized for
 #endif
 
 namespace mp3 {
