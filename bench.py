@@ -49,7 +49,7 @@ MOMENTS_TRAFFIC_BYTES = 4 * (124.231168e6 + 1053.384e6)
 # DRAM bytes per launch of the tensor-core contraction (BF16x3) at lognormal_200k: ncu capture
 # at 50 000 galaxies (profiles/contract_tc_bf16x3_lognormal_50k.md) scaled to 200 000 centres
 # (the traffic is the moment stream, proportional to the centres). None whenever it changes.
-CONTRACT_TRAFFIC_BYTES = 4 * (1.033375e9 + 8.868096e6)
+CONTRACT_TRAFFIC_BYTES = 4 * (1.066084e9 + 9.231360e6)
 
 
 def flops_per_pair(n_max: int) -> int:

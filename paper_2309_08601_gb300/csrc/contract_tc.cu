@@ -37,7 +37,7 @@ namespace mp3 {
 
 namespace tc {
 
-constexpr int kConvWarps = 8;                  // converter warps: two per TMEM lane quarter
+constexpr int kConvWarps = 16;                 // converter warps: four per TMEM lane quarter
 constexpr int kThreads = (kConvWarps + 2) * 32;  // + one TMA warp + one MMA warp
 constexpr int kM = 128;         // MMA rows (TMEM lanes)
 constexpr int kMaxGroups = 8;   // groups stacked in one tile
@@ -142,7 +142,7 @@ struct TcArgs {
     ContractArgs<float> c;
     int groups;   // nz^3 * groups_per_zt(n_max): index space of the partial sums
     int gt;       // groups per tile
-    int npad;     // MMA N: gt * 2 nb rounded up to 16
+    int npad;     // MMA N: gt * 2 nb rounded up to 32 (8 TMEM columns per converter part and load)
     int nbp;      // bins padded to even (the moment rows)
     int ta, tw;   // tiles per component of Upsilon (n_max + 1 orders) and of N (2 n_max + 1 orders)
     int fixed_slices;  // > 0: this many centre slices instead of the automatic choice
@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 2) contract_tc_kernel(const __grid_c
         // ================= converter warps
         // this thread's conversion items, the same in every stage: item = (word column kw, group
         // t, bin b); 4 consecutive lanes fill one 16-byte core row, 8 lane quads fill 8 rows
-        constexpr int kItems = 2;  // KW * ng * nb <= 8 * 64 = 512 = 2 * kConvWarps * 32
+        constexpr int kItems = (8 * 64 + kConvWarps * 32 - 1) / (kConvWarps * 32);  // KW * ng * nb <= 8 * 64
         const int TB = ng * nb;
         const int items = L::KW * TB;
         uint32_t i_ore[kItems], i_oim[kItems];
@@ -713,7 +713,7 @@ cudaError_t launch_contract_tc(const ContractArgs<float>& c, bool tf32, int n_sm
     a.groups = c.nz * c.nz * c.nz * groups_per_zt(c.n_max);
     a.gt = std::min(tc::kMaxGroups, tc::kM / (2 * c.nb));
     if (a.gt < 1) return cudaErrorInvalidValue;
-    a.npad = ((a.gt * 2 * c.nb + 15) / 16) * 16;
+    a.npad = ((a.gt * 2 * c.nb + 31) / 32) * 32;
     a.nbp = nb_pad(c.nb);
     a.ta = (c.n_max + 1 + a.gt - 1) / a.gt;
     a.tw = (2 * c.n_max + 1 + a.gt - 1) / a.gt;

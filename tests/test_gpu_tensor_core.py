@@ -64,7 +64,7 @@ def test_tensor_core_is_deterministic(gpu, noise2k):
 
 @pytest.mark.parametrize("n_bins,n_max", [(1, 0), (7, 5), (33, 3), (64, 2), (4, 50)])
 def test_tile_shapes(gpu, orc, n_bins, n_max):
-    """Groups per tile 8 (n_bins <= 8), 1 with a ragged N (33 bins: 66 rows, N = 80) and the
+    """Groups per tile 8 (n_bins <= 8), 1 with a ragged N (33 bins: 66 rows, N = 96) and the
     full 128 rows (64 bins); largest order."""
     rng = np.random.default_rng(100 + n_bins)
     n = 500
