@@ -175,6 +175,27 @@ def oracle_sample(cat, setup, theta, target_s: float, seed: int = 0):
     return pairs, sec, k, oracle.num_threads()
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -356,6 +377,8 @@ def run_gpu(args):
             "data": "synthetic (seeded lognormal Kaiser-Squires shear + shape noise)",
             "config": workload_config(args.workload, p, args.precision),
             "catalogs_per_s": cat_per_s, "pairs_per_catalog": pairs,
+            "pairs_per_s_moments_kernel": pairs / (k1_ms / 1e3),
+            "moment_terms_per_s": pairs * ((2 * nmax + 3) + (2 * nmax + 1)) / (k1_ms / 1e3),
             "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
             "roofline": roofline, "roofline_contract": roofline_contract, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks.summary()}
@@ -381,10 +404,19 @@ def run_gpu(args):
                              "map3_rel_err_vs_fp64": err, "m8_rel_err_vs_fp64": err_all}
 
     if rank == 0 and args.cpu_baseline:
+        import oracle
         pr, sec, k, threads = oracle_sample(cat, setup, theta, target_s=args.cpu_s)
         line["cpu_baseline"] = {"value": pr / sec, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": "%d random centres (all %d galaxies as neighbours), whole "
-                                          "path, %.1f s" % (k, cat.n, sec)}
+                                          "path, %.1f s" % (k, cat.n, sec),
+                                "cpu_model": cpu_model()}
+        if threads > 1:
+            oracle.set_num_threads(1)
+            pr1, sec1, k1, _ = oracle_sample(cat, setup, theta, target_s=args.cpu_s / 2, seed=1)
+            oracle.set_num_threads(threads)
+            line["cpu_baseline"]["one_core"] = {
+                "value": pr1 / sec1, "unit": UNIT, "cores": 1,
+                "sample": "%d random centres, whole path, %.1f s" % (k1, sec1)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     est.close()

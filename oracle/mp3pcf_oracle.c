@@ -847,3 +847,15 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* threads of the following parallel regions (timing on a given number of host cores) */
+int orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}

@@ -77,6 +77,7 @@ def lib():
             "orc_combine8": [P, P],
             "orc_brute": [P, I64, P, P, P, P, P, P, C.c_int32, P, P, P, P, P, P],
             "orc_num_threads": [],
+            "orc_set_num_threads": [C.c_int32],
         }.items():
             f = getattr(_lib, name)
             f.argtypes = args
@@ -100,6 +101,11 @@ def _check(rc: int, ok=(0,)):
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops from now on (for timing on n host cores)."""
+    return lib().orc_set_num_threads(int(n))
 
 
 def edges(s: Setup):
@@ -284,4 +290,4 @@ def pipeline(s: Setup, cat, theta_ap, centres: Optional[np.ndarray] = None) -> R
 
 __all__ = ["Setup", "build_oracle", "edges", "moments", "count_pairs", "contract",
            "edge_correct", "degenerate_correction", "to_gamma", "to_map3", "filter_F", "cen_factor", "combine8", "brute",
-           "pipeline", "num_threads", "Result", "Brute"]
+           "pipeline", "num_threads", "set_num_threads", "Result", "Brute"]

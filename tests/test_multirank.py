@@ -80,3 +80,16 @@ def test_reference_arm_under_torchrun_two_ranks():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_oracle_thread_count_and_cpu_model():
+    """The CPU baseline is timed on all host cores and on one core; the thread count is set on
+    the oracle and restored, and the CPU model is reported."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    oracle.build_oracle()
+    n = oracle.num_threads()
+    assert oracle.set_num_threads(1) == 1 and oracle.num_threads() == 1
+    assert oracle.set_num_threads(n) == n
+    assert isinstance(bench.cpu_model(), str) and bench.cpu_model()
