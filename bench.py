@@ -175,6 +175,39 @@ def oracle_sample(cat, setup, theta, target_s: float, seed: int = 0):
     return pairs, sec, k, oracle.num_threads()
 
 
+def measure_batch(api, n_real: int, precision: str, stream):
+    """n_real realisations of the tomographic batching workload through one mp3pcf_run_batch call
+    (the largest catalog sizes the workspace, the others replay a captured CUDA graph)."""
+    import torch
+    from paper_2309_08601_gb300 import synth
+    tp = synth.WORKLOADS["tomo_64x5_lognormal"]
+    bset = dict(n_bins=tp["n_bins"], theta_min=tp["theta_min"], theta_max=tp["theta_max"],
+                n_max=tp["n_max"], n_z=tp["n_z"])
+    bth = [[t, t, t] for t in tp["theta_ap"]]
+    cats = [synth.make_tomographic_catalog(1000 + r, side=tp["side"], n_z=tp["n_z"]) for r in range(n_real)]
+    devs = [api.catalog_to_device(c) for c in cats]
+    ext = (0, 0, int(np.ceil(tp["side"] / synth.QUANTUM)), int(np.ceil(tp["side"] / synth.QUANTUM)))
+    with api.Estimator(**bset, precision=precision, stream=stream) as eb:
+        pairs = 0
+        for d in devs:  # untimed: the pair counter holds the last accumulation
+            eb.accumulate_moments(*d[:5], zbin=d[5])
+            pairs += eb.counts()[1]
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        m8 = eb.run_batch([d[:5] + (d[5],) for d in devs], ext, bth, use_graphs=True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        sec = t0.elapsed_time(t1) / 1e3
+        launches, inst = eb.graph_stats()
+        finite = bool(torch.isfinite(m8).all())
+    return {"workload": "tomo_64x5_lognormal: %d of the 64 realisations, 5 z-bins of U{50k..400k} "
+                        "galaxies on 300', all 125 Z-triplets" % n_real,
+            "galaxies": [int(c.n) for c in cats], "pairs": int(pairs), "seconds": sec,
+            "catalogs_per_s": n_real / sec, "pairs_per_s": pairs / sec,
+            "graph_launches": launches, "graph_instantiations": inst, "m8_finite": finite}
+
+
 def cpu_model() -> str:
     """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
     import platform
@@ -403,6 +436,11 @@ def run_gpu(args):
                              "speedup_of_measured_path": (cat_per_s / world) * s64,
                              "map3_rel_err_vs_fp64": err, "m8_rel_err_vs_fp64": err_all}
 
+    # ---- the batching form: whole tomographic realisations (5 z-bins of 50k-400k galaxies)
+    # through mp3pcf_run_batch with CUDA graphs, rank 0; pairs counted by an untimed pass
+    if rank == 0 and args.batch_realisations > 0:
+        line["batch"] = measure_batch(api, args.batch_realisations, args.precision, stream)
+
     if rank == 0 and args.cpu_baseline:
         import oracle
         pr, sec, k, threads = oracle_sample(cat, setup, theta, target_s=args.cpu_s)
@@ -441,6 +479,8 @@ def main(argv=None):
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work sampled")
+    ap.add_argument("--batch-realisations", type=int, default=2,
+                    help="tomographic realisations timed through mp3pcf_run_batch (0: skip)")
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     ap.add_argument("--k1-traffic", type=float, default=None,
                     help="DRAM bytes per moments launch (default: the committed ncu figure, at "

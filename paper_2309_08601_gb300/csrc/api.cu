@@ -292,6 +292,14 @@ __global__ void k_mask_flags(int64_t n, const uint8_t* __restrict__ mask, int* _
         f[i] = mask ? (mask[i] != 0) : 1;
 }
 
+// first centre of each z-bin in the centre list (sorted by z-bin first): the sorted index of the
+// first galaxy of z-bin z is cell_start[z * ncells], its rank among the centres crank[] of it
+__global__ void k_zrange(int nz, int64_t ncells, const int* __restrict__ cell_start, const int* __restrict__ crank,
+                         int* __restrict__ zrange)
+{
+    for (int z = threadIdx.x; z <= nz; z += blockDim.x) zrange[z] = crank[cell_start[(int64_t)z * ncells]];
+}
+
 // centre list in sorted order and, for each centre, its row in galaxy-index order
 __global__ void k_centres(int64_t n, const int* __restrict__ perm, const int* __restrict__ cflag,
                           const int* __restrict__ crank, const int* __restrict__ orank,
@@ -360,6 +368,7 @@ struct mp3pcf_ctx {
     DevBuf G, W, pairs, partial, singular, m3partial, ccoef;
     DevBuf gG, gW, gv, gw, adjscratch;  // adjoint workspace
     DevBuf degen;                       // exclude_degenerate sums per (centre, z, bin)
+    DevBuf zrange;                      // [nz + 1] centre range of each z-bin
     // tracing: per-stage event pairs and kernel-launch counts
     bool timing = false;
     int64_t launches[6] = {0, 0, 0, 0, 0, 0};
@@ -686,6 +695,12 @@ static mp3pcf_status accumulate_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq,
                                                     ctx->crank.as<int>(), ctx->orank.as<int>(),
                                                     ctx->centre_idx.as<int>(), ctx->crow.as<int>());
     MP3_CK(cudaGetLastError());
+    if (nz > 1) {
+        MP3_CK(ctx->zrange.ensure(sizeof(int) * (nz + 1)));
+        k_zrange<<<1, 32, 0, st>>>(nz, g.ncells, ctx->count.as<int>(), ctx->crank.as<int>(), ctx->zrange.as<int>());
+        MP3_CK(cudaGetLastError());
+        ctx->launches[ST_SORT] += 1;
+    }
     int nc = (int)n;
     if (mask) {
         MP3_CK(cudaMemcpyAsync(&nc, ctx->crank.as<int>() + n, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -791,7 +806,7 @@ mp3pcf_status mp3pcf_contract_multipoles(mp3pcf_ctx* ctx, double* d_upsilon, dou
         const bool tf32 = c.precision == MP3PCF_FP32_TF32X3;
         ContractArgs<float> a{ctx->G.as<cx<float>>(), ctx->W.as<cx<float>>(), ctx->pay.as<Pay<float>>(),
                               ctx->zs.as<uint8_t>(), ctx->centre_idx.as<int>(), (int32_t)nc, nz, nb, c.n_max,
-                              0, nullptr};
+                              0, nullptr, nz > 1 ? ctx->zrange.as<int>() : nullptr};
         int splits = 0;
         unsigned long long* errw = ctx->pairs.as<unsigned long long>() + 1;
         MP3_CK(launch_contract_tc(a, tf32, ctx->n_sm, nullptr, errw, &splits, true, c.contract_slices, 0, ctx->st));
@@ -818,13 +833,13 @@ mp3pcf_status mp3pcf_contract_multipoles(mp3pcf_ctx* ctx, double* d_upsilon, dou
         ContractArgs<double> a{ctx->G.as<cx<double>>(), ctx->W.as<cx<double>>(), ctx->pay.as<Pay<double>>(),
                                ctx->zs.as<uint8_t>(),
                                ctx->centre_idx.as<int>(), (int32_t)nc, nz, nb, c.n_max, splits,
-                               ctx->partial.as<double>()};
+                               ctx->partial.as<double>(), nz > 1 ? ctx->zrange.as<int>() : nullptr};
         e = launch_contract_f64(a, ctx->st);
     } else {
         ContractArgs<float> a{ctx->G.as<cx<float>>(), ctx->W.as<cx<float>>(), ctx->pay.as<Pay<float>>(),
                               ctx->zs.as<uint8_t>(),
                               ctx->centre_idx.as<int>(), (int32_t)nc, nz, nb, c.n_max, splits,
-                              ctx->partial.as<double>()};
+                              ctx->partial.as<double>(), nz > 1 ? ctx->zrange.as<int>() : nullptr};
         e = launch_contract_f32(a, ctx->st);
     }
     MP3_CK(e);

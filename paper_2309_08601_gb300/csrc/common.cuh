@@ -111,6 +111,9 @@ struct ContractArgs {
     int32_t nz, nb, n_max;
     int32_t splits;
     double* partial;  // [splits][groups][nb*nb][2]
+    // device [nz + 1]: the centres of z-bin z are [zrange[z], zrange[z + 1]) of the centre list
+    // (sorted by z-bin); nullptr: every centre (one z-bin)
+    const int32_t* zrange;
 };
 
 cudaError_t launch_contract_f32(const ContractArgs<float>& a, cudaStream_t st);

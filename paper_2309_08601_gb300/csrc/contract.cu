@@ -48,9 +48,11 @@ __global__ void __launch_bounds__(kThreads) contract_kernel(const ContractArgs<T
     const size_t plane = (size_t)a.n_centres * nz * nbp;  // stride between order slots
     const cx<T>* src = kind < 4 ? a.G : a.W;
     const int nbb = nb * nb;
-    const int per = (a.n_centres + a.splits - 1) / a.splits;
-    const int c0 = sl * per;
-    const int c1 = min(a.n_centres, c0 + per);
+    // only the centres of z-bin z1 (a contiguous range of the z-sorted centre list)
+    const int zc0 = a.zrange ? a.zrange[z1] : 0, zc1 = a.zrange ? a.zrange[z1 + 1] : a.n_centres;
+    const int per = (zc1 - zc0 + a.splits - 1) / a.splits;
+    const int c0 = min(zc1, zc0 + sl * per);
+    const int c1 = min(zc1, c0 + per);
 
     double accd[MAXO][2];
 #pragma unroll

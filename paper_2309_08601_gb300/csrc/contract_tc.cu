@@ -310,9 +310,11 @@ __global__ void __launch_bounds__(kThreads, 2) contract_tc_kernel(const __grid_c
     const int iy0 = (sy > 0 ? ay : ay - (ng - 1)) + off;
     const CUtensorMap* mapM = kind < 4 ? &mapG : &mapW;
 
+    // slices of the centres of z-bin z1 (a contiguous range of the z-sorted centre list)
     const int sl = blockIdx.y, slices = gridDim.y;
-    const int per = (A.n_centres + slices - 1) / slices;
-    const int c0 = min(A.n_centres, sl * per), c1 = min(A.n_centres, c0 + per);
+    const int zc0 = A.zrange ? A.zrange[z1] : 0, zc1 = A.zrange ? A.zrange[z1 + 1] : A.n_centres;
+    const int per = (zc1 - zc0 + slices - 1) / slices;
+    const int c0 = min(zc1, zc0 + sl * per), c1 = min(zc1, c0 + per);
     const int ntiles = (c1 - c0 + KT - 1) / KT;
     const int nchains = (ntiles + kFlush - 1) / kFlush;
 
