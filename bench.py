@@ -175,6 +175,31 @@ def oracle_sample(cat, setup, theta, target_s: float, seed: int = 0):
     return pairs, sec, k, oracle.num_threads()
 
 
+def measure_adjoint(api, est, dev, theta, stream):
+    """One forward and one backward of the differentiable Map^3 (api.map3) on the bench catalog,
+    each timed with CUDA events (after one untimed pair); L = sum of the Map^3 measures."""
+    import torch
+    xq, yq, g1, g2, w = dev[:5]
+
+    def once():
+        a1, a2, aw = (t.clone().requires_grad_(True) for t in (g1, g2, w))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        m8 = api.map3(est, xq, yq, a1, a2, aw, theta)
+        L = m8[..., 0].sum()
+        ev[1].record(stream)
+        L.backward()
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), a1.grad, float(L.detach())
+
+    once()
+    fwd, bwd, gr, L = once()
+    return {"loss": "sum of Map^3 over the apertures", "forward_ms": fwd, "backward_ms": bwd,
+            "backward_over_forward": bwd / fwd, "grad_finite": bool(torch.isfinite(gr).all()),
+            "kernels": "map3/to_gamma/edge_correct adjoints, contraction adjoint, moments adjoint"}
+
+
 def measure_batch(api, n_real: int, precision: str, stream):
     """n_real realisations of the tomographic batching workload through one mp3pcf_run_batch call
     (the largest catalog sizes the workspace, the others replay a captured CUDA graph)."""
@@ -436,6 +461,10 @@ def run_gpu(args):
                              "speedup_of_measured_path": (cat_per_s / world) * s64,
                              "map3_rel_err_vs_fp64": err, "m8_rel_err_vs_fp64": err_all}
 
+    # ---- the differentiation form on the same catalog: forward + backward through api.map3
+    if rank == 0 and args.adjoint:
+        line["adjoint"] = measure_adjoint(api, est, dev, theta, stream)
+
     # ---- the batching form: whole tomographic realisations (5 z-bins of 50k-400k galaxies)
     # through mp3pcf_run_batch with CUDA graphs, rank 0; pairs counted by an untimed pass
     if rank == 0 and args.batch_realisations > 0:
@@ -479,6 +508,8 @@ def main(argv=None):
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work sampled")
+    ap.add_argument("--no-adjoint", dest="adjoint", action="store_false",
+                    help="skip the forward + backward timing of the differentiable Map^3")
     ap.add_argument("--batch-realisations", type=int, default=2,
                     help="tomographic realisations timed through mp3pcf_run_batch (0: skip)")
     ap.add_argument("--ref-step-s", type=float, default=8.0)

@@ -14,9 +14,11 @@ namespace mp3 {
 // Solves A X = B in shared memory for one system (D x D complex A, D x 4 complex B, both
 // overwritten; X in B): Gaussian elimination with partial pivoting (largest |pivot|, lowest row
 // on ties) by the whole block, back substitution by four warps. Returns true if a pivot was zero.
+// Per elimination step: the pivot by a warp-shuffle argmax and one pass over the warps' results,
+// the multipliers A_rk / A_kk once per row (stored in the finished column k), then the update.
 __device__ bool block_solve4(cx<double>* A, cx<double>* B, int D, double* red_v, int* red_i, int* s_bad)
 {
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, nw = blockDim.x >> 5;
     for (int k = 0; k < D && !*s_bad; ++k) {
         double best = -1.0;
         int bi = D;
@@ -28,24 +30,31 @@ __device__ bool block_solve4(cx<double>* A, cx<double>* B, int D, double* red_v,
                 bi = r;
             }
         }
-        red_v[tid] = best;
-        red_i[tid] = bi;
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if (tid < s) {
-                const double ov = red_v[tid + s];
-                const int oi = red_i[tid + s];
-                if (ov > red_v[tid] || (ov == red_v[tid] && oi < red_i[tid])) {
-                    red_v[tid] = ov;
-                    red_i[tid] = oi;
-                }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) {
+                best = ov;
+                bi = oi;
             }
-            __syncthreads();
         }
-        const int piv = red_i[0];
-        const bool zero = !(red_v[0] > 0.0);
+        if (lane == 0) {
+            red_v[tid >> 5] = best;
+            red_i[tid >> 5] = bi;
+        }
         __syncthreads();
-        if (zero) {
+        double pv = red_v[0];
+        int piv = red_i[0];
+        for (int w = 1; w < nw; ++w) {
+            const double ov = red_v[w];
+            const int oi = red_i[w];
+            if (ov > pv || (ov == pv && oi < piv)) {
+                pv = ov;
+                piv = oi;
+            }
+        }
+        if (!(pv > 0.0)) {
             if (tid == 0) *s_bad = 1;
             __syncthreads();
             break;
@@ -64,10 +73,12 @@ __device__ bool block_solve4(cx<double>* A, cx<double>* B, int D, double* red_v,
         }
         __syncthreads();
         const cx<double> akk = A[(size_t)k * D + k];
+        for (int r = k + 1 + tid; r < D; r += blockDim.x) A[(size_t)r * D + k] = cdiv(A[(size_t)r * D + k], akk);
+        __syncthreads();
         const int rows = D - k - 1, cols = D - k - 1 + 4;
         for (int idx = tid; idx < rows * cols; idx += blockDim.x) {
             const int r = k + 1 + idx / cols, jj = idx % cols;
-            const cx<double> f = cdiv(A[(size_t)r * D + k], akk);
+            const cx<double> f = A[(size_t)r * D + k];
             if (jj < D - k - 1) {
                 const int j = k + 1 + jj;
                 A[(size_t)r * D + j] = csub(A[(size_t)r * D + j], cmul(f, A[(size_t)k * D + j]));
@@ -79,7 +90,7 @@ __device__ bool block_solve4(cx<double>* A, cx<double>* B, int D, double* red_v,
         __syncthreads();
     }
     const bool bad = *s_bad != 0;
-    const int warp = tid >> 5, lane = tid & 31;
+    const int warp = tid >> 5;
     if (!bad && warp < 4) {
         const int mu = warp;
         for (int k = D - 1; k >= 0; --k) {
