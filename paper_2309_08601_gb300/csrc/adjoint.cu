@@ -223,9 +223,9 @@ __global__ void __launch_bounds__(128) contract_adjoint_coef(const AdjArgs<T> a)
         }
     }
     if (act) {
-        a.gv[2 * (size_t)d] += gv.x;
-        a.gv[2 * (size_t)d + 1] += gv.y;
-        a.gw[d] += gw;
+        a.gvw[4 * (size_t)d] += gv.x;
+        a.gvw[4 * (size_t)d + 1] += gv.y;
+        a.gvw[4 * (size_t)d + 2] += gw;
     }
 }
 
@@ -246,17 +246,16 @@ __device__ __forceinline__ long long fdiv(long long a, long long b)
     return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
 }
 
-template <typename T>
-__device__ __forceinline__ void atomic_add_t(T* p, T v);
-template <>
-__device__ __forceinline__ void atomic_add_t<float>(float* p, float v)
+// adds (re grad v, im grad v, grad w) to a galaxy's 16-byte (FP32) or 32-byte (FP64) slot
+__device__ __forceinline__ void atomic_add_vw(float* p, float vr, float vi, float w)
 {
-    atomicAdd(p, v);
+    atomicAdd(reinterpret_cast<float4*>(p), make_float4(vr, vi, w, 0.0f));
 }
-template <>
-__device__ __forceinline__ void atomic_add_t<double>(double* p, double v)
+__device__ __forceinline__ void atomic_add_vw(double* p, double vr, double vi, double w)
 {
-    atomicAdd(p, v);
+    atomicAdd(p, vr);
+    atomicAdd(p + 1, vi);
+    atomicAdd(p + 2, w);
 }
 
 template <typename T>
@@ -278,10 +277,18 @@ __device__ __forceinline__ cx<double> unit_dir<double>(long long dx, long long d
 
 constexpr int kPairWarps = 4;
 
-// Calls f(k, dx, dy) on the calling lane for every galaxy k of redshift bin z whose squared
-// separation r2 from the centre (px, py) lies in [r2lo, r2hi); the warp walks, row by row of the
-// cell grid, the one or two runs of cells that meet the annulus (cells wholly inside the inner
-// radius are skipped), one candidate per lane. Must be called by the whole warp.
+// one Horner step p <- p x + c in four fused multiply-adds
+template <typename T>
+__device__ __forceinline__ cx<T> horner_step(cx<T> p, cx<T> x, cx<T> c)
+{
+    return {fma(p.x, x.x, fma(-p.y, x.y, c.x)), fma(p.x, x.y, fma(p.y, x.x, c.y))};
+}
+
+// Walks the candidates of redshift bin z around the centre (px, py): the warp goes row by row of
+// the cell grid over the one or two runs of cells that meet the annulus (cells wholly inside the
+// inner radius are skipped), 32 candidates at a time, one per lane, and calls f(in, k, dx, dy) on
+// every lane of the warp at every step (warp-uniform), with in = whether galaxy k's squared
+// separation r2 lies in [r2lo, r2hi). Must be called by the whole warp.
 template <typename F>
 __device__ __forceinline__ void for_each_in_annulus(const GridDesc& g, const int32_t* __restrict__ cell_start,
                                                     const int2* __restrict__ pos, long long px, long long py,
@@ -320,18 +327,29 @@ __device__ __forceinline__ void for_each_in_annulus(const GridDesc& g, const int
         for (int sgi = 0; sgi < nseg; ++sgi) {
             const int k0 = cell_start[key0 + segs[sgi][0]];
             const int k1 = cell_start[key0 + segs[sgi][1] + 1];
-            for (int k = k0 + lane; k < k1; k += 32) {
-                const int2 qk = pos[k];
-                const long long dx = (long long)qk.x - px, dy = (long long)qk.y - py;
-                const long long r2 = dx * dx + dy * dy;
-                if (r2 >= r2lo && r2 < r2hi) f(k, dx, dy);
+            for (int kb = k0; kb < k1; kb += 32) {
+                const int k = kb + lane;
+                long long dx = 0, dy = 0;
+                bool in = false;
+                if (k < k1) {
+                    const int2 qk = pos[k];
+                    dx = (long long)qk.x - px;
+                    dy = (long long)qk.y - py;
+                    const long long r2 = dx * dx + dy * dy;
+                    in = r2 >= r2lo && r2 < r2hi;
+                }
+                f(in, k, dx, dy);
             }
         }
     }
 }
 
 // warp per centre (grid-stride); per bin the warp stages the centre's adjoint moments of every Z
-// in shared memory and walks the annulus
+// in shared memory and walks the annulus. The members found are queued (unit vector, galaxy) in
+// the warp's shared-memory queue and evaluated 32 at a time, one per lane, so that no lane idles
+// through the polynomial evaluations while others hold a member.
+constexpr int kQueue = 64;
+
 template <typename T>
 __global__ void __launch_bounds__(kPairWarps * 32) moments_adjoint_pairs(const AdjArgs<T> a)
 {
@@ -339,7 +357,11 @@ __global__ void __launch_bounds__(kPairWarps * 32) moments_adjoint_pairs(const A
     const int nb = a.nb, nz = a.nz, nmax = a.n_max, nbp = nb_pad(nb);
     const int MG = 2 * nmax + 3, MW = 2 * nmax + 1, o = nmax + 3;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
     cx<T>* co = reinterpret_cast<cx<T>*>(smem_raw) + (size_t)warp * nz * (MG + MW);  // [z][MG + MW]
+    cx<T>* qz = reinterpret_cast<cx<T>*>(smem_raw) + (size_t)kPairWarps * nz * (MG + MW) + (size_t)warp * kQueue;
+    int* qk = reinterpret_cast<int*>(reinterpret_cast<cx<T>*>(smem_raw) + (size_t)kPairWarps * nz * (MG + MW) +
+                                     (size_t)kPairWarps * kQueue) + warp * kQueue;
     const size_t plane = (size_t)a.n_centres * nz * nbp;
     for (int c = blockIdx.x * kPairWarps + warp; c < a.n_centres; c += gridDim.x * kPairWarps) {
         const int d = a.centre_idx[c];
@@ -355,32 +377,52 @@ __global__ void __launch_bounds__(kPairWarps * 32) moments_adjoint_pairs(const A
             for (int z = 0; z < nz; ++z) {
                 const cx<T>* gg = co + (size_t)z * (MG + MW);
                 const cx<T>* gw = gg + MG;
-                for_each_in_annulus(a.g, a.cell_start, a.pos, p.x, p.y, a.e2q[b], a.e2q[b + 1], z, lane,
-                                    [&](int k, long long dx, long long dy) {
-                    const cx<T> zz = unit_dir<T>(dx, dy);
+                // grad v_k += sum_m gG_m e^{-i m phi}, grad w_k += Re sum_m gW_m e^{-i m phi} for the
+                // queued member e
+                auto eval = [&](int e) {
+                    const cx<T> zz = qz[e];
+                    const int k = qk[e];
                     const cx<T> u{zz.x, -zz.y};
-                    // m >= 0 part of sum_m gG_m u^m (Horner in u)
+                    // m >= 0 part of sum_m gG_m u^m (Horner in u, P <- P u + c: four FMAs)
                     cx<T> P{T(0), T(0)};
-                    for (int mm = nmax - 1; mm >= 0; --mm) {
-                        P = cmul(P, u);
-                        P = cadd(P, gg[o + mm]);
-                    }
-                    // m < 0 part: sum_{j >= 1} gG_{-j} z^j (Horner in z)
-                    cx<T> Q{T(0), T(0)};
-                    for (int j = nmax + 3; j >= 1; --j) {
-                        Q = cadd(Q, gg[o - j]);
-                        Q = cmul(Q, zz);
-                    }
+#pragma unroll 4
+                    for (int mm = nmax - 1; mm >= 0; --mm) P = horner_step(P, u, gg[o + mm]);
+                    // m < 0 part: sum_{j >= 1} gG_{-j} z^j = z (gG_{-1} + z (gG_{-2} + ...))
+                    cx<T> Q = gg[o - (nmax + 3)];
+#pragma unroll 4
+                    for (int j = nmax + 2; j >= 1; --j) Q = horner_step(Q, zz, gg[o - j]);
+                    Q = cmul(Q, zz);
                     // W: sum_m gW_m u^m
                     cx<T> Rw{T(0), T(0)};
-                    for (int mm = 2 * nmax; mm >= 0; --mm) {
-                        Rw = cmul(Rw, u);
-                        Rw = cadd(Rw, gw[mm]);
+#pragma unroll 4
+                    for (int mm = 2 * nmax; mm >= 0; --mm) Rw = horner_step(Rw, u, gw[mm]);
+                    atomic_add_vw(a.gvw + 4 * (size_t)k, P.x + Q.x, P.y + Q.y, Rw.x);
+                };
+                int qn = 0;  // queued members (warp-uniform), < 32 between steps
+                for_each_in_annulus(a.g, a.cell_start, a.pos, p.x, p.y, a.e2q[b], a.e2q[b + 1], z, lane,
+                                    [&](bool in, int k, long long dx, long long dy) {
+                    const unsigned m = __ballot_sync(0xffffffffu, in);
+                    if (in) {
+                        const int slot = qn + __popc(m & lt_mask);
+                        qz[slot] = unit_dir<T>(dx, dy);
+                        qk[slot] = k;
                     }
-                    atomic_add_t<T>(&a.gv[2 * (size_t)k], P.x + Q.x);
-                    atomic_add_t<T>(&a.gv[2 * (size_t)k + 1], P.y + Q.y);
-                    atomic_add_t<T>(&a.gw[k], Rw.x);
+                    qn += __popc(m);
+                    if (qn >= 32) {
+                        __syncwarp();
+                        eval(lane);
+                        __syncwarp();
+                        if (lane < qn - 32) {
+                            qz[lane] = qz[32 + lane];
+                            qk[lane] = qk[32 + lane];
+                        }
+                        __syncwarp();
+                        qn -= 32;
+                    }
                 });
+                __syncwarp();
+                if (lane < qn) eval(lane);
+                __syncwarp();
             }
         }
     }
@@ -389,18 +431,18 @@ __global__ void __launch_bounds__(kPairWarps * 32) moments_adjoint_pairs(const A
 // caller order, v = w (gamma_1 + i gamma_2): dL/dgamma_1 = w Re grad v, dL/dgamma_2 = w Im grad v,
 // dL/dw = (direct) + Re grad v gamma_1 + Im grad v gamma_2; ADDS to the caller's arrays
 template <typename T>
-__global__ void adjoint_finish(int64_t n, const int* __restrict__ perm, const T* __restrict__ gv,
-                               const T* __restrict__ gw, const float* __restrict__ g1, const float* __restrict__ g2,
+__global__ void adjoint_finish(int64_t n, const int* __restrict__ perm, const T* __restrict__ gvw,
+                               const float* __restrict__ g1, const float* __restrict__ g2,
                                const float* __restrict__ w, float* __restrict__ dg1, float* __restrict__ dg2,
                                float* __restrict__ dw)
 {
     for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < n; d += (int64_t)gridDim.x * blockDim.x) {
         const int i = perm[d];
-        const T vr = gv[2 * d], vi = gv[2 * d + 1];
+        const T vr = gvw[4 * d], vi = gvw[4 * d + 1];
         const T wi = (T)w[i];
         if (dg1) dg1[i] += (float)(wi * vr);
         if (dg2) dg2[i] += (float)(wi * vi);
-        if (dw) dw[i] += (float)(gw[d] + vr * (T)g1[i] + vi * (T)g2[i]);
+        if (dw) dw[i] += (float)(gvw[4 * d + 2] + vr * (T)g1[i] + vi * (T)g2[i]);
     }
 }
 
@@ -408,8 +450,7 @@ template <typename T>
 static cudaError_t run(const AdjArgs<T>& a, int64_t n, const int* perm, const float* g1, const float* g2,
                        const float* w, float* dg1, float* dg2, float* dw, int n_sm, cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(a.gv, 0, sizeof(T) * 2 * (size_t)n, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(a.gw, 0, sizeof(T) * (size_t)n, st);
+    cudaError_t e = cudaMemsetAsync(a.gvw, 0, sizeof(T) * 4 * (size_t)n, st);
     if (e != cudaSuccess) return e;
     if (a.n_centres > 0) {
         const int MG = 2 * a.n_max + 3, MW = 2 * a.n_max + 1;
@@ -421,7 +462,8 @@ static cudaError_t run(const AdjArgs<T>& a, int64_t n, const int* perm, const fl
         if (e != cudaSuccess) return e;
         contract_adjoint_coef<T><<<(a.n_centres + 127) / 128, 128, sm_coef, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        const size_t sm_pair = sizeof(cx<T>) * (size_t)kPairWarps * a.nz * (MG + MW);
+        const size_t sm_pair = sizeof(cx<T>) * (size_t)kPairWarps * (a.nz * (MG + MW) + kQueue) +
+                               sizeof(int) * (size_t)kPairWarps * kQueue;
         e = set_smem_attr(moments_adjoint_pairs<T>, sm_pair);
         if (e != cudaSuccess) return e;
         const int blocks = (int)std::min<int64_t>((a.n_centres + kPairWarps - 1) / kPairWarps, (int64_t)n_sm * 32);
@@ -429,7 +471,7 @@ static cudaError_t run(const AdjArgs<T>& a, int64_t n, const int* perm, const fl
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)n_sm * 16));
-    adjoint_finish<T><<<gb, 256, 0, st>>>(n, perm, a.gv, a.gw, g1, g2, w, dg1, dg2, dw);
+    adjoint_finish<T><<<gb, 256, 0, st>>>(n, perm, a.gvw, g1, g2, w, dg1, dg2, dw);
     return cudaGetLastError();
 }
 
@@ -456,7 +498,8 @@ __global__ void __launch_bounds__(kPairWarps * 32) degenerate_moments(const AdjA
             for (int z = 0; z < nz; ++z) {
                 T s[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
                 for_each_in_annulus(a.g, a.cell_start, a.pos, p.x, p.y, a.e2q[b], a.e2q[b + 1], z, lane,
-                                    [&](int k, long long dx, long long dy) {
+                                    [&](bool in, int k, long long dx, long long dy) {
+                    if (!in) return;
                     const cx<T> zz = unit_dir<T>(dx, dy);
                     const cx<T> u{zz.x, -zz.y};
                     const cx<T> u2 = cmul(u, u), u6 = cmul(cmul(u2, u2), u2);

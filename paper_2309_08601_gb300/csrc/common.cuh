@@ -161,8 +161,8 @@ struct AdjArgs {
     const double* gnorm;        // dL/dN [z3][2n_max+1][nb][nb] complex
     cx<T>* gG;                  // dL/dG, dL/dW (order-major, like G and W)
     cx<T>* gW;
-    T* gv;                      // [n][2] dL/dv per sorted galaxy (v = w gamma)
-    T* gw;                      // [n] direct dL/dw per sorted galaxy
+    T* gvw;                     // [n][4] per sorted galaxy: dL/dv (re, im; v = w gamma), direct
+                                // dL/dw, unused (16 bytes: one vector atomic per pair in FP32)
 };
 
 cudaError_t launch_moments_adjoint_f32(const AdjArgs<float>& a, int64_t n, const int* perm, const float* g1,
