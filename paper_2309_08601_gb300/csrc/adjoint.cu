@@ -62,6 +62,20 @@ __device__ __forceinline__ void cfma(cx<T>& acc, cx<T> a, cx<T> b)
 
 constexpr int kTileC = 32;  // centres per block
 
+// the gradient tables of AdjArgs (tabX transposed so that the X role reads consecutive bins)
+template <typename T>
+__global__ void grad_tables(const AdjArgs<T> a, int64_t n_ups_groups, int64_t total)
+{
+    const int nb = a.nb, nbb = nb * nb;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = i / nbb;
+        const int o = (int)(i % nbb), b1 = o / nb, b2 = o % nb;
+        const cx<double> v = g < n_ups_groups ? ldd(a.gups, i) : ldd(a.gnorm, i - n_ups_groups * nbb);
+        a.tabY[i] = to_t<T>(v);
+        a.tabX[g * nbb + (int64_t)b2 * nb + b1] = to_t<T>(v);
+    }
+}
+
 // grid: x = centre tiles, y = output order slot (G slots 0..MG-1, then W slots); thread per
 // (centre, z, bin) output element
 template <typename T>
@@ -85,25 +99,29 @@ __global__ void __launch_bounds__(256) contract_adjoint_moments(const AdjArgs<T>
         const cx<T> cw{pv.w, T(0)};
         const size_t crow = (size_t)c * nz;
         // X role: output at b1 = b, partner Y at order slot qy of Z zo; returns
-        // conj(coef) sum_b2 grad y(b, b2) conj(Y(b2))
-        auto roleX = [&](const cx<T>* M, const double* gy, size_t gbase, int zo, int qy, bool yconj, cx<T> coef) {
+        // conj(coef) sum_b2 grad y(b, b2) conj(Y(b2)) (grad y from the transposed table: the
+        // lanes, consecutive in b, read consecutive elements)
+        const size_t nbb = (size_t)nb * nb, n_off = (size_t)nz * nz * nz * 4 * NN * nbb;
+        auto roleX = [&](const cx<T>* M, size_t gbase, int zo, int qy, bool yconj, cx<T> coef) {
             cx<T> s{T(0), T(0)};
             const cx<T>* Y = M + (size_t)qy * plane + (crow + zo) * nbp;
+            const cx<T>* gt = a.tabX + gbase + b;
             for (int b2 = 0; b2 < nb; ++b2) {
                 cx<T> y = Y[b2];
                 if (!yconj) y.y = -y.y;  // conj(Y) (conj(conj(G)) = G when Y enters conjugated)
-                cfma(s, to_t<T>(ldd(gy, gbase + (size_t)b * nb + b2)), y);
+                cfma(s, gt[(size_t)b2 * nb], y);
             }
             return cmul(s, cconj(coef));
         };
         // Y role: output at b2 = b, partner X at order slot qx of Z zo
-        auto roleY = [&](const cx<T>* M, const double* gy, size_t gbase, int zo, int qx, bool xconj, cx<T> coef) {
+        auto roleY = [&](const cx<T>* M, size_t gbase, int zo, int qx, bool xconj, cx<T> coef) {
             cx<T> s{T(0), T(0)};
             const cx<T>* X = M + (size_t)qx * plane + (crow + zo) * nbp;
+            const cx<T>* gt = a.tabY + gbase + b;
             for (int b1 = 0; b1 < nb; ++b1) {
                 cx<T> x = X[b1];
                 if (!xconj) x.y = -x.y;
-                cfma(s, to_t<T>(ldd(gy, gbase + (size_t)b1 * nb + b)), x);
+                cfma(s, gt[(size_t)b1 * nb], x);
             }
             return cmul(s, cconj(coef));
         };
@@ -116,26 +134,26 @@ __global__ void __launch_bounds__(256) contract_adjoint_moments(const AdjArgs<T>
                 int n;
                 // kind 0: G_{n-3}(b1) G_{-n-3}(b2), coef -v
                 n = m + 3;
-                if (n >= 0 && n <= nmax) acc = cadd(acc, roleX(a.G, a.gups, ub(ztX, 0, n), zo, -n - 3 + o, false, c0));
+                if (n >= 0 && n <= nmax) acc = cadd(acc, roleX(a.G, ub(ztX, 0, n), zo, -n - 3 + o, false, c0));
                 n = -m - 3;
-                if (n >= 0 && n <= nmax) acc = cadd(acc, roleY(a.G, a.gups, ub(ztY, 0, n), zo, n - 3 + o, false, c0));
+                if (n >= 0 && n <= nmax) acc = cadd(acc, roleY(a.G, ub(ztY, 0, n), zo, n - 3 + o, false, c0));
                 // kind 1: G_{n-1}(b1) G_{-n-1}(b2), coef -conj(v)
                 n = m + 1;
-                if (n >= 0 && n <= nmax) acc = cadd(acc, roleX(a.G, a.gups, ub(ztX, 1, n), zo, -n - 1 + o, false, c1));
+                if (n >= 0 && n <= nmax) acc = cadd(acc, roleX(a.G, ub(ztX, 1, n), zo, -n - 1 + o, false, c1));
                 n = -m - 1;
-                if (n >= 0 && n <= nmax) acc = cadd(acc, roleY(a.G, a.gups, ub(ztY, 1, n), zo, n - 1 + o, false, c1));
+                if (n >= 0 && n <= nmax) acc = cadd(acc, roleY(a.G, ub(ztY, 1, n), zo, n - 1 + o, false, c1));
                 // kind 2: conj(G_{-n-1}(b1)) G_{-n-3}(b2), coef -v
                 n = -m - 1;
                 if (n >= 0 && n <= nmax)
-                    acc = cadd(acc, cconj(roleX(a.G, a.gups, ub(ztX, 2, n), zo, -n - 3 + o, false, c0)));
+                    acc = cadd(acc, cconj(roleX(a.G, ub(ztX, 2, n), zo, -n - 3 + o, false, c0)));
                 n = -m - 3;
-                if (n >= 0 && n <= nmax) acc = cadd(acc, roleY(a.G, a.gups, ub(ztY, 2, n), zo, -n - 1 + o, true, c0));
+                if (n >= 0 && n <= nmax) acc = cadd(acc, roleY(a.G, ub(ztY, 2, n), zo, -n - 1 + o, true, c0));
                 // kind 3: G_{n-3}(b1) conj(G_{n-1}(b2)), coef -v
                 n = m + 3;
-                if (n >= 0 && n <= nmax) acc = cadd(acc, roleX(a.G, a.gups, ub(ztX, 3, n), zo, n - 1 + o, true, c0));
+                if (n >= 0 && n <= nmax) acc = cadd(acc, roleX(a.G, ub(ztX, 3, n), zo, n - 1 + o, true, c0));
                 n = m + 1;
                 if (n >= 0 && n <= nmax)
-                    acc = cadd(acc, cconj(roleY(a.G, a.gups, ub(ztY, 3, n), zo, n - 3 + o, false, c0)));
+                    acc = cadd(acc, cconj(roleY(a.G, ub(ztY, 3, n), zo, n - 3 + o, false, c0)));
             }
             a.gG[(size_t)q * plane + (crow + z) * nbp + b] = acc;
         } else {
@@ -143,36 +161,53 @@ __global__ void __launch_bounds__(256) contract_adjoint_moments(const AdjArgs<T>
             for (int zo = 0; zo < nz; ++zo) {
                 const int ztX = (z1 * nz + z) * nz + zo, ztY = (z1 * nz + zo) * nz + z;
                 // N_n: w W_n(b1) conj(W_n(b2))
-                const size_t nX = (((size_t)ztX * NW + n) * nb) * nb, nY = (((size_t)ztY * NW + n) * nb) * nb;
-                acc = cadd(acc, roleX(a.W, a.gnorm, nX, zo, n, true, cw));
-                acc = cadd(acc, cconj(roleY(a.W, a.gnorm, nY, zo, n, false, cw)));
+                const size_t nX = n_off + (((size_t)ztX * NW + n) * nb) * nb;
+                const size_t nY = n_off + (((size_t)ztY * NW + n) * nb) * nb;
+                acc = cadd(acc, roleX(a.W, nX, zo, n, true, cw));
+                acc = cadd(acc, cconj(roleY(a.W, nY, zo, n, false, cw)));
             }
             a.gW[(size_t)n * plane + (crow + z) * nbp + b] = acc;
         }
     }
 }
 
-// grad of every centre's own coefficient: thread per centre, the group's dL/dy staged in shared
-// memory; adds dL/dv (re, im) and dL/dw of the centre's sorted galaxy
+// grad of every centre's own coefficient: a warp per centre (kCoefCentres centres per warp), lanes
+// over b1; per group the block stages the group's transposed dL/dy in shared memory (skipped when
+// none of the block's centres is in the group's Z1) and each warp forms
+// gc = sum_b1 conj(X(b1)) sum_b2 dL/dy(b1, b2) conj(Y(b2)) (partner rows read as warp broadcasts),
+// then adds dL/dv (re, im) and dL/dw of the centre's sorted galaxy
+constexpr int kCoefWarps = 8, kCoefCentres = 4;
+
 template <typename T>
-__global__ void __launch_bounds__(128) contract_adjoint_coef(const AdjArgs<T> a)
+__global__ void __launch_bounds__(kCoefWarps * 32) contract_adjoint_coef(const AdjArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cx<T>* gy = reinterpret_cast<cx<T>*>(smem_raw);  // [nb][nb]
-    const int nb = a.nb, nz = a.nz, nmax = a.n_max, nbp = nb_pad(nb);
+    cx<T>* gyT = reinterpret_cast<cx<T>*>(smem_raw);  // [nb][nb]: gyT[b2 * nb + b1]
+    const int nb = a.nb, nz = a.nz, nmax = a.n_max, nbp = nb_pad(nb), nbb = nb * nb;
     const int o = nmax + 3, NN = nmax + 1, NW = 2 * nmax + 1;
     const int per_zt = groups_per_zt(nmax);
     const size_t plane = (size_t)a.n_centres * nz * nbp;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool act = c < a.n_centres;
-    const int d = act ? a.centre_idx[c] : 0;
-    const int zc = act && a.zs ? (int)a.zs[d] : 0;
-    cx<T> gv{T(0), T(0)};
-    T gw = T(0);
+    const int64_t nU = (int64_t)nz * nz * nz * 4 * NN;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cbase = (blockIdx.x * kCoefWarps + warp) * kCoefCentres;
+    int dd[kCoefCentres], zc[kCoefCentres];
+    cx<T> gv[kCoefCentres];
+    T gw[kCoefCentres];
+    unsigned zmask = 0;  // z-bins of this warp's centres
+#pragma unroll
+    for (int j = 0; j < kCoefCentres; ++j) {
+        const int c = cbase + j;
+        dd[j] = c < a.n_centres ? a.centre_idx[c] : -1;
+        zc[j] = dd[j] >= 0 ? (a.zs ? (int)a.zs[dd[j]] : 0) : -1;
+        if (zc[j] >= 0) zmask |= 1u << (zc[j] & 31);
+        gv[j] = cx<T>{T(0), T(0)};
+        gw[j] = T(0);
+    }
     const int groups = nz * nz * nz * per_zt;
     for (int g = 0; g < groups; ++g) {
         const int zt = g / per_zt, loc = g % per_zt;
         const int z1 = zt / (nz * nz), z2 = (zt / nz) % nz, z3 = zt % nz;
+        if (!__syncthreads_or((zmask >> (z1 & 31)) & 1u)) continue;  // no centre of the block in Z1
         int kind, n;
         if (loc < 4 * NN) {
             kind = loc / NN;
@@ -181,12 +216,10 @@ __global__ void __launch_bounds__(128) contract_adjoint_coef(const AdjArgs<T> a)
             kind = 4;
             n = loc - 4 * NN;
         }
-        const double* src = kind < 4 ? a.gups + 2 * ((((size_t)zt * 4 + kind) * NN + n) * nb * nb)
-                                      : a.gnorm + 2 * (((size_t)zt * NW + n) * nb * nb);
+        const int64_t tg = kind < 4 ? ((int64_t)zt * 4 + kind) * NN + n : nU + (int64_t)zt * NW + n;
+        const cx<T>* src = a.tabX + tg * nbb;  // already transposed: [b2][b1]
+        for (int i = threadIdx.x; i < nbb; i += blockDim.x) gyT[i] = src[i];
         __syncthreads();
-        for (int i = threadIdx.x; i < nb * nb; i += blockDim.x) gy[i] = cx<T>{(T)src[2 * i], (T)src[2 * i + 1]};
-        __syncthreads();
-        if (!act || zc != z1) continue;
         int qx, qy;
         bool xc = false, yc = false;
         switch (kind) {
@@ -197,35 +230,49 @@ __global__ void __launch_bounds__(128) contract_adjoint_coef(const AdjArgs<T> a)
             default: qx = n; qy = n; yc = true; break;
         }
         const cx<T>* M = kind < 4 ? a.G : a.W;
-        const cx<T>* X = M + (size_t)qx * plane + ((size_t)c * nz + z2) * nbp;
-        const cx<T>* Y = M + (size_t)qy * plane + ((size_t)c * nz + z3) * nbp;
-        // gc = sum_b1 conj(X(b1)) sum_b2 gy(b1, b2) conj(Y(b2))
-        cx<T> gc{T(0), T(0)};
-        for (int b1 = 0; b1 < nb; ++b1) {
-            cx<T> s{T(0), T(0)};
-            for (int b2 = 0; b2 < nb; ++b2) {
-                cx<T> y = Y[b2];
-                if (!yc) y.y = -y.y;
-                cfma(s, gy[b1 * nb + b2], y);
+#pragma unroll
+        for (int j = 0; j < kCoefCentres; ++j) {
+            if (zc[j] != z1) continue;  // warp-uniform
+            const int c = cbase + j;
+            const cx<T>* X = M + (size_t)qx * plane + ((size_t)c * nz + z2) * nbp;
+            const cx<T>* Y = M + (size_t)qy * plane + ((size_t)c * nz + z3) * nbp;
+            cx<T> part{T(0), T(0)};
+            for (int b1 = lane; b1 < nb; b1 += 32) {
+                cx<T> sy{T(0), T(0)};
+                for (int b2 = 0; b2 < nb; ++b2) {
+                    cx<T> y = Y[b2];
+                    if (!yc) y.y = -y.y;
+                    cfma(sy, gyT[b2 * nb + b1], y);
+                }
+                cx<T> x = X[b1];
+                if (!xc) x.y = -x.y;
+                cfma(part, x, sy);
             }
-            cx<T> x = X[b1];
-            if (!xc) x.y = -x.y;
-            cfma(gc, x, s);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                part.x += __shfl_xor_sync(0xffffffffu, part.x, off);
+                part.y += __shfl_xor_sync(0xffffffffu, part.y, off);
+            }
+            if (kind == 4) {
+                gw[j] += part.x;  // c = w
+            } else if (kind == 1) {
+                gv[j].x -= part.x;  // c = -conj(v): grad v = -conj(grad c)
+                gv[j].y += part.y;
+            } else {
+                gv[j].x -= part.x;  // c = -v
+                gv[j].y -= part.y;
+            }
         }
-        if (kind == 4) {
-            gw += gc.x;  // c = w
-        } else if (kind == 1) {
-            gv.x -= gc.x;  // c = -conj(v): grad v = -conj(grad c)
-            gv.y += gc.y;
-        } else {
-            gv.x -= gc.x;  // c = -v
-            gv.y -= gc.y;
-        }
+        __syncthreads();
     }
-    if (act) {
-        a.gvw[4 * (size_t)d] += gv.x;
-        a.gvw[4 * (size_t)d + 1] += gv.y;
-        a.gvw[4 * (size_t)d + 2] += gw;
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < kCoefCentres; ++j)
+            if (dd[j] >= 0) {
+                a.gvw[4 * (size_t)dd[j]] += gv[j].x;
+                a.gvw[4 * (size_t)dd[j] + 1] += gv[j].y;
+                a.gvw[4 * (size_t)dd[j] + 2] += gw[j];
+            }
     }
 }
 
@@ -455,12 +502,17 @@ static cudaError_t run(const AdjArgs<T>& a, int64_t n, const int* perm, const fl
     if (a.n_centres > 0) {
         const int MG = 2 * a.n_max + 3, MW = 2 * a.n_max + 1;
         dim3 g1d((a.n_centres + kTileC - 1) / kTileC, MG + MW);
+        const int64_t z3 = (int64_t)a.nz * a.nz * a.nz, nbb = (int64_t)a.nb * a.nb;
+        const int64_t nU = z3 * 4 * (a.n_max + 1), tot = (nU + z3 * (2 * a.n_max + 1)) * nbb;
+        grad_tables<T><<<(unsigned)std::min<int64_t>((tot + 255) / 256, (int64_t)n_sm * 16), 256, 0, st>>>(a, nU, tot);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         contract_adjoint_moments<T><<<g1d, 256, 0, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const size_t sm_coef = sizeof(cx<T>) * (size_t)a.nb * a.nb;
         e = set_smem_attr(contract_adjoint_coef<T>, sm_coef);
         if (e != cudaSuccess) return e;
-        contract_adjoint_coef<T><<<(a.n_centres + 127) / 128, 128, sm_coef, st>>>(a);
+        constexpr int per_block = kCoefWarps * kCoefCentres;
+        contract_adjoint_coef<T><<<(a.n_centres + per_block - 1) / per_block, kCoefWarps * 32, sm_coef, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const size_t sm_pair = sizeof(cx<T>) * (size_t)kPairWarps * (a.nz * (MG + MW) + kQueue) +
                                sizeof(int) * (size_t)kPairWarps * kQueue;

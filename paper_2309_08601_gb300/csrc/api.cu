@@ -366,7 +366,7 @@ struct mp3pcf_ctx {
     DevBuf bb, key, count, fill, scan_sums, scan_total, perm, pos, pay, zs;
     DevBuf cflag, crank, oflag, orank, centre_idx, crow;
     DevBuf G, W, pairs, partial, singular, m3partial, ccoef;
-    DevBuf gG, gW, gv, adjscratch;  // adjoint workspace
+    DevBuf gG, gW, gv, gtab, adjscratch;  // adjoint workspace
     DevBuf degen;                       // exclude_degenerate sums per (centre, z, bin)
     DevBuf zrange;                      // [nz + 1] centre range of each z-bin
     // tracing: per-stage event pairs and kernel-launch counts
@@ -546,7 +546,7 @@ mp3pcf_status mp3pcf_destroy(mp3pcf_ctx* ctx)
                       &ctx->pos, &ctx->pay, &ctx->zs, &ctx->cflag,
                       &ctx->crank, &ctx->oflag, &ctx->orank, &ctx->centre_idx, &ctx->crow,
                       &ctx->G, &ctx->W, &ctx->pairs, &ctx->partial, &ctx->singular,
-                      &ctx->m3partial, &ctx->ccoef, &ctx->gG, &ctx->gW, &ctx->gv,
+                      &ctx->m3partial, &ctx->ccoef, &ctx->gG, &ctx->gW, &ctx->gv, &ctx->gtab,
                       &ctx->adjscratch, &ctx->degen, &ctx->bups, &ctx->bnorm, &ctx->bgam, &ctx->bgcen, &ctx->berr};
     for (DevBuf* b : bufs) b->release();
     if (ctx->batch_st) cudaStreamDestroy(ctx->batch_st);
@@ -1202,6 +1202,8 @@ static mp3pcf_status moments_adjoint_t(mp3pcf_ctx* ctx, const double* gups, cons
     const int64_t n = ctx->n, nc = ctx->n_centres;
     const int nz = c.n_z, nb = c.n_bins;
     MP3_CK(ctx->gv.ensure(sizeof(T) * 4 * (size_t)std::max<int64_t>(n, 1)));
+    const size_t ngroups = (size_t)nz * nz * nz * (4 * (c.n_max + 1) + 2 * c.n_max + 1);
+    MP3_CK(ctx->gtab.ensure(2 * sizeof(cx<T>) * ngroups * nb * nb));
     if (nc > 0) {
         MP3_CK(ctx->gG.ensure(sizeof(cx<T>) * (size_t)(2 * c.n_max + 3) * nc * nz * nb_pad(nb)));
         MP3_CK(ctx->gW.ensure(sizeof(cx<T>) * (size_t)(2 * c.n_max + 1) * nc * nz * nb_pad(nb)));
@@ -1225,6 +1227,8 @@ static mp3pcf_status moments_adjoint_t(mp3pcf_ctx* ctx, const double* gups, cons
     a.gG = ctx->gG.as<cx<T>>();
     a.gW = ctx->gW.as<cx<T>>();
     a.gvw = ctx->gv.as<T>();
+    a.tabX = ctx->gtab.as<cx<T>>();
+    a.tabY = a.tabX + ngroups * nb * nb;
     StageScope sc(ctx, ST_MOMENTS);
     ctx->launches[ST_MOMENTS] += nc > 0 ? 4 : 1;
     cudaError_t e;

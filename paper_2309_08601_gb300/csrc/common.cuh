@@ -159,6 +159,10 @@ struct AdjArgs {
     const cx<T>* W;
     const double* gups;         // dL/dUpsilon [z3][4][n_max+1][nb][nb] complex
     const double* gnorm;        // dL/dN [z3][2n_max+1][nb][nb] complex
+    // the same gradients in the moment precision, group by group (the Upsilon groups in the order
+    // of gups, then the N groups): tabY[g][b1][b2] as stored, tabX[g][b2][b1] transposed
+    cx<T>* tabX;
+    cx<T>* tabY;
     cx<T>* gG;                  // dL/dG, dL/dW (order-major, like G and W)
     cx<T>* gW;
     T* gvw;                     // [n][4] per sorted galaxy: dL/dv (re, im; v = w gamma), direct

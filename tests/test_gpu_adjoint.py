@@ -99,6 +99,32 @@ def test_whole_chain_against_oracle_autograd(gpu, case1, precision, tol):
     assert max(errs) < tol
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 2e-6), ("bf16x3", 1e-4)])
+def test_tomographic_chain_against_oracle_autograd(gpu, orc, precision, tol):
+    """Two z-bins (all 8 Z-triplets, each centre contracted only in its own Z1): the whole chain's
+    gradient against the oracle's FP64 autograd."""
+    from oracle import torch_oracle as to
+    rng = np.random.default_rng(44)
+    n = 300
+    cat = hand_catalog(rng.uniform(0, 14, (n, 2)), rng.normal(0, .3, n) + 1j * rng.normal(0, .3, n),
+                       rng.uniform(0.5, 1.5, n), rng.integers(0, 2, n))
+    setup = dict(S1, n_z=2)
+    mo = to.Map3Oracle(orc.Setup(**setup), cat, TH1, chunk_pairs=20_000)
+    c = np.random.default_rng(6).normal(size=(8, len(TH1), 8))
+    o1, o2, ow, _ = mo.grad(*_cpu64(cat), c)
+    dev = gpu.catalog_to_device(cat)
+    g1 = dev[2].clone().requires_grad_(True)
+    g2 = dev[3].clone().requires_grad_(True)
+    w = dev[4].clone().requires_grad_(True)
+    with gpu.Estimator(**setup, precision=precision) as est:
+        m8 = gpu.map3(est, dev[0], dev[1], g1, g2, w, TH1, zbin=dev[5])
+        (torch.as_tensor(c, device="cuda") * m8).sum().backward()
+    errs = [rel_err(g1.grad.cpu().numpy(), o1.numpy()), rel_err(g2.grad.cpu().numpy(), o2.numpy()),
+            rel_err(w.grad.cpu().numpy(), ow.numpy())]
+    print(precision, "tomographic gradient errors vs FP64 autograd oracle", errs)
+    assert max(errs) < tol
+
+
 def _euler(api, cat, setup, theta, precision, c):
     dev = api.catalog_to_device(cat)
     g1 = dev[2].clone().requires_grad_(True)
