@@ -385,43 +385,56 @@ cudaError_t launch_to_gamma(const PostArgs& p, const double* gam, int projection
 }
 
 // Adjoint of to_gamma: dL/dGamma_n = sum_k dL/dGamma(phi_k) conj(R(phi_k)) e^{-i n phi_k}, with
-// R the centroid factor (projection 1) or 1. Thread per (Z-triplet, mu, b1, b2, n); overwrites.
-__global__ void to_gamma_adjoint_kernel(const PostArgs p, const double* __restrict__ gphi, int proj,
-                                        double* __restrict__ ggam)
+// R the centroid factor (projection 1) or 1. Block per (Z-triplet, mu, b1, b2): the n_phi weighted
+// gradients h_k = dL/dGamma(phi_k) conj(R(phi_k)) are formed once in shared memory, then a thread
+// per n sums h_k e^{-i n phi_k} over k (the same order of terms as a direct sum); overwrites.
+constexpr int kTgaThreads = 128;
+
+__global__ void __launch_bounds__(kTgaThreads) to_gamma_adjoint_kernel(const PostArgs p,
+                                                                      const double* __restrict__ gphi, int proj,
+                                                                      double* __restrict__ ggam)
 {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<double>* h = reinterpret_cast<cx<double>*>(smem_raw);  // [n_phi]
     const int nb = p.nb, nmax = p.n_max, D = 2 * nmax + 1, np = p.n_phi;
-    const int64_t total = (int64_t)p.nz * p.nz * p.nz * 4 * D * nb * nb;
-    const cx<double>* Gp = reinterpret_cast<const cx<double>*>(gphi);
-    cx<double>* O = reinterpret_cast<cx<double>*>(ggam);
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int b2 = (int)(t % nb), b1 = (int)((t / nb) % nb);
-        const int nn = (int)((t / ((int64_t)nb * nb)) % D) - nmax;
-        const int64_t zm = t / ((int64_t)nb * nb * D);  // zt * 4 + mu
-        const cx<double>* g = Gp + (((size_t)zm * nb + b1) * nb + b2) * np;
-        double sr = 0.0, si = 0.0;
-        for (int k = 0; k < np; ++k) {
+    const int64_t sys = blockIdx.x;  // ((zt * 4 + mu) * nb + b1) * nb + b2
+    const int b2 = (int)(sys % nb), b1 = (int)((sys / nb) % nb);
+    const int64_t zm = sys / ((int64_t)nb * nb);  // zt * 4 + mu
+    const cx<double>* g = reinterpret_cast<const cx<double>*>(gphi) + sys * np;
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        cx<double> v = g[k];
+        if (proj) {
             double s, c;
             sincospi((2.0 * k + 1.0) / np, &s, &c);
+            v = cmul(v, cconj(centroid_factor((int)(zm % 4), p.nodes[b1], p.nodes[b2], cx<double>{c, s})));
+        }
+        h[k] = v;
+    }
+    __syncthreads();
+    cx<double>* O = reinterpret_cast<cx<double>*>(ggam);
+    for (int i = threadIdx.x; i < D; i += blockDim.x) {
+        const int nn = i - nmax;
+        double sr = 0.0, si = 0.0;
+        for (int k = 0; k < np; ++k) {
             double sn, cn;
             sincospi((double)nn * (2.0 * k + 1.0) / np, &sn, &cn);
-            cx<double> v = cmul(g[k], cx<double>{cn, -sn});  // e^{-i n phi_k}
-            if (proj) v = cmul(v, cconj(centroid_factor((int)(zm % 4), p.nodes[b1], p.nodes[b2], cx<double>{c, s})));
+            const cx<double> v = cmul(h[k], cx<double>{cn, -sn});  // e^{-i n phi_k}
             sr += v.x;
             si += v.y;
         }
-        O[t] = cx<double>{sr, si};
+        O[((size_t)zm * D + i) * nb * nb + (size_t)b1 * nb + b2] = cx<double>{sr, si};
     }
 }
 
 cudaError_t launch_to_gamma_adjoint(const PostArgs& p, const double* gphi, int projection, double* ggam,
                                     cudaStream_t st)
 {
-    const int64_t total = (int64_t)p.nz * p.nz * p.nz * 4 * (2 * p.n_max + 1) * p.nb * p.nb;
-    int64_t blocks = (total + 255) / 256;
-    if (blocks > 65535) blocks = 65535;
-    if (blocks < 1) blocks = 1;
-    to_gamma_adjoint_kernel<<<(unsigned)blocks, 256, 0, st>>>(p, gphi, projection, ggam);
+    const int64_t systems = (int64_t)p.nz * p.nz * p.nz * 4 * p.nb * p.nb;
+    if (systems < 1) return cudaSuccess;
+    const size_t smem = sizeof(cx<double>) * (size_t)p.n_phi;
+    cudaError_t e = set_smem_attr(to_gamma_adjoint_kernel, smem);
+    if (e != cudaSuccess) return e;
+    to_gamma_adjoint_kernel<<<(unsigned)systems, kTgaThreads, smem, st>>>(p, gphi, projection, ggam);
     return cudaGetLastError();
 }
 
