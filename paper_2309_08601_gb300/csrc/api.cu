@@ -134,15 +134,21 @@ __global__ void k_bbox(int64_t n, const int32_t* __restrict__ xq, const int32_t*
     }
 }
 
+// Cell key of every galaxy. With a fixed extent the positions are only validated on the device
+// (k_validate raises the error word, reported as EINVAL after the call) and the pipeline runs on;
+// a position outside the extent or a z-bin >= nz is therefore clamped to the grid here, so that
+// no index derived from it leaves the cell arrays.
 __global__ void k_keys(int64_t n, const int32_t* __restrict__ xq, const int32_t* __restrict__ yq,
-                       const uint8_t* __restrict__ zb, GridDesc g, int* __restrict__ key,
+                       const uint8_t* __restrict__ zb, int nz, GridDesc g, int* __restrict__ key,
                        int* __restrict__ count)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int cx_ = (int)(((long long)xq[i] - g.x0) / g.side);
-        const int cy_ = (int)(((long long)yq[i] - g.y0) / g.side);
-        const int k = (zb ? (int)zb[i] : 0) * g.ncells + cy_ * g.ncx + cx_;
+        const long long dx = max(0LL, (long long)xq[i] - g.x0), dy = max(0LL, (long long)yq[i] - g.y0);
+        const int cx_ = (int)min(dx / g.side, (long long)g.ncx - 1);
+        const int cy_ = (int)min(dy / g.side, (long long)g.ncy - 1);
+        const int z = zb ? min((int)zb[i], nz - 1) : 0;
+        const int k = z * g.ncells + cy_ * g.ncx + cx_;
         key[i] = k;
         atomicAdd(&count[k], 1);
     }
@@ -272,7 +278,7 @@ __global__ void k_gather(int64_t n, const int* __restrict__ perm, const int32_t*
                          const float* __restrict__ g2, const float* __restrict__ w,
                          const uint8_t* __restrict__ zb, const uint8_t* __restrict__ mask,
                          int2* __restrict__ pos, Pay<T>* __restrict__ pay,
-                         uint8_t* __restrict__ zs, int* __restrict__ cflag)
+                         uint8_t* __restrict__ zs, int* __restrict__ cflag, int nz)
 {
     for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < n;
          d += (int64_t)gridDim.x * blockDim.x) {
@@ -280,7 +286,7 @@ __global__ void k_gather(int64_t n, const int* __restrict__ perm, const int32_t*
         pos[d] = make_int2(xq[i], yq[i]);
         const T wi = (T)w[i];
         pay[d] = Pay<T>{wi * (T)g1[i], wi * (T)g2[i], wi, T(0)};
-        zs[d] = zb ? zb[i] : 0;
+        zs[d] = zb ? (uint8_t)min((int)zb[i], nz - 1) : 0;  // clamped like the cell key (k_keys)
         cflag[d] = mask ? (mask[i] != 0) : 1;
     }
 }
@@ -675,7 +681,7 @@ static mp3pcf_status accumulate_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq,
     MP3_CK(ctx->crow.ensure(sizeof(int) * n));
     MP3_CK(cudaMemsetAsync(ctx->fill.p, 0, sizeof(int) * (K + 1), st));
     ctx->launches[ST_SORT] += 6;
-    k_keys<<<grid1d(n, ctx->n_sm), 256, 0, st>>>(n, xq, yq, zb, g, ctx->key.as<int>(), ctx->fill.as<int>());
+    k_keys<<<grid1d(n, ctx->n_sm), 256, 0, st>>>(n, xq, yq, zb, nz, g, ctx->key.as<int>(), ctx->fill.as<int>());
     MP3_CK(cudaGetLastError());
     if (mp3pcf_status s = scan_exclusive(ctx, ctx->fill.as<int>(), ctx->count.as<int>(), K)) return s;
     MP3_CK(cudaMemsetAsync(ctx->fill.p, 0, sizeof(int) * (K + 1), st));
@@ -684,7 +690,7 @@ static mp3pcf_status accumulate_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq,
     k_cell_order<<<grid1d(K, ctx->n_sm), 256, 0, st>>>(K, ctx->count.as<int>(), ctx->perm.as<int>());
     k_gather<T><<<grid1d(n, ctx->n_sm), 256, 0, st>>>(
         n, ctx->perm.as<int>(), xq, yq, g1, g2, w, zb, mask, ctx->pos.as<int2>(), ctx->pay.as<Pay<T>>(),
-        ctx->zs.as<uint8_t>(), ctx->cflag.as<int>());
+        ctx->zs.as<uint8_t>(), ctx->cflag.as<int>(), nz);
     MP3_CK(cudaGetLastError());
 
     // ---- centre list (sorted order) and each centre's row in galaxy-index order
