@@ -839,6 +839,100 @@ int orc_brute(const orc_cfg* c, int64_t n, const int32_t* xq, const int32_t* yq,
     return ORC_OK;
 }
 
+/* ---- Direct estimator of the third-order aperture mass (Sec. 5.3, Eq. MapDirectEstimator) ----
+ * At the aperture centre c (arcmin) and aperture radii (t1, t2, t3):
+ *   num = sum over distinct i, j, k of w_i w_j w_k Q_t1(r_i) Q_t2(r_j) Q_t3(r_k) gt_i gt_j gt_k
+ *   den = the same sum without the tangential shears,
+ * with r_i = |x_i - c|, gt_i = Re(gamma(x_i; zeta_i)) the tangential shear about c (zeta_i the
+ * polar angle of x_i - c, Eq. gammatx_def) and Q the filter of Eq. CrittendenQ,
+ * Q_t(r) = r^2 / (4 pi t^4) exp(-r^2 / (2 t^2)); galaxies farther than rcut from c are left out.
+ * The estimate at c is num / den; <M_ap^3> is its average over apertures. */
+
+static double q_filter(double r, double t)
+{
+    return r * r / (4.0 * M_PI * t * t * t * t) * exp(-r * r / (2.0 * t * t));
+}
+
+/* the per-galaxy factors a_l = w Q_tl gt (with_gt) or w Q_tl, l = 0..2; 0 beyond rcut */
+static int direct_factors(double x, double y, float g1, float g2, float w, double cx, double cy,
+                          const double* th, double rcut, int with_gt, double a[3])
+{
+    const double dx = x - cx, dy = y - cy, r = sqrt(dx * dx + dy * dy);
+    if (r > rcut || r == 0.0) {
+        a[0] = a[1] = a[2] = 0.0;
+        return 0;
+    }
+    double gt = 1.0;
+    if (with_gt) gt = creal(proj((double)g1 + I * (double)g2, atan2(dy, dx), 0));
+    for (int l = 0; l < 3; ++l) a[l] = (double)w * q_filter(r, th[l]) * gt;
+    return 1;
+}
+
+/* Literal triple loop over distinct (i, j, k): the definition, for tiny catalogs. */
+int orc_map3_direct_brute(int64_t n, const int32_t* xq, const int32_t* yq, const float* g1,
+                          const float* g2, const float* w, double quantum, double cx, double cy,
+                          const double* th, double rcut, double* num, double* den)
+{
+    double sn = 0.0, sd = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double ai[3], bi[3];
+        direct_factors(xq[i] * quantum, yq[i] * quantum, g1[i], g2[i], w[i], cx, cy, th, rcut, 1, ai);
+        direct_factors(xq[i] * quantum, yq[i] * quantum, g1[i], g2[i], w[i], cx, cy, th, rcut, 0, bi);
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double aj[3], bj[3];
+            direct_factors(xq[j] * quantum, yq[j] * quantum, g1[j], g2[j], w[j], cx, cy, th, rcut, 1, aj);
+            direct_factors(xq[j] * quantum, yq[j] * quantum, g1[j], g2[j], w[j], cx, cy, th, rcut, 0, bj);
+            for (int64_t k = 0; k < n; ++k) {
+                if (k == i || k == j) continue;
+                double ak[3], bk[3];
+                direct_factors(xq[k] * quantum, yq[k] * quantum, g1[k], g2[k], w[k], cx, cy, th, rcut, 1, ak);
+                direct_factors(xq[k] * quantum, yq[k] * quantum, g1[k], g2[k], w[k], cx, cy, th, rcut, 0, bk);
+                sn += ai[0] * aj[1] * ak[2];
+                sd += bi[0] * bj[1] * bk[2];
+            }
+        }
+    }
+    *num = sn;
+    *den = sd;
+    return ORC_OK;
+}
+
+/* The same sums for many apertures in O(n) each: for factors a, b, c of the three slots,
+ *   sum_{i,j,k distinct} a_i b_j c_k = A B C - (AB) C - (AC) B - (BC) A + 2 (ABC)
+ * (inclusion-exclusion over the coincidences i = j, i = k, j = k; A = sum a_i, AB = sum a_i b_i,
+ * ...). out[t][0..1] = (num, den) of aperture t; centres [n_cen][2] arcmin. */
+int orc_map3_direct(int64_t n, const int32_t* xq, const int32_t* yq, const float* g1, const float* g2,
+                    const float* w, double quantum, int64_t n_cen, const double* centres,
+                    const double* th, double rcut, double* out)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t t = 0; t < n_cen; ++t) {
+        double s[2][7] = {{0}};
+        for (int64_t i = 0; i < n; ++i) {
+            for (int with_gt = 1; with_gt >= 0; --with_gt) {
+                double a[3];
+                if (!direct_factors(xq[i] * quantum, yq[i] * quantum, g1[i], g2[i], w[i], centres[2 * t],
+                                    centres[2 * t + 1], th, rcut, with_gt, a))
+                    break;
+                double* q = s[1 - with_gt];
+                q[0] += a[0];
+                q[1] += a[1];
+                q[2] += a[2];
+                q[3] += a[0] * a[1];
+                q[4] += a[0] * a[2];
+                q[5] += a[1] * a[2];
+                q[6] += a[0] * a[1] * a[2];
+            }
+        }
+        for (int v = 0; v < 2; ++v) {
+            const double* q = s[v];
+            out[2 * t + v] = q[0] * q[1] * q[2] - q[3] * q[2] - q[4] * q[1] - q[5] * q[0] + 2.0 * q[6];
+        }
+    }
+    return ORC_OK;
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

@@ -77,6 +77,9 @@ def lib():
             "orc_combine8": [P, P],
             "orc_brute": [P, I64, P, P, P, P, P, P, C.c_int32, P, P, P, P, P, P],
             "orc_num_threads": [],
+            "orc_map3_direct_brute": [I64, P, P, P, P, P, C.c_double, C.c_double, C.c_double, P, C.c_double,
+                                      P, P],
+            "orc_map3_direct": [I64, P, P, P, P, P, C.c_double, I64, P, P, C.c_double, P],
             "orc_set_num_threads": [C.c_int32],
         }.items():
             f = getattr(_lib, name)
@@ -97,6 +100,29 @@ def _check(rc: int, ok=(0,)):
     if rc not in ok:
         raise RuntimeError("oracle call failed with status %d" % rc)
     return rc
+
+
+def map3_direct(cat, centres, theta, rcut_factor: float = 4.0, brute: bool = False) -> np.ndarray:
+    """Numerator and denominator of the direct <M_ap^3> estimator (Sec. 5.3, Eq.
+    MapDirectEstimator) at every aperture centre [n][2] (arcmin) for the radii theta (3,):
+    [n][2]. Galaxies beyond rcut_factor * max(theta) from a centre are left out. brute: the
+    literal triple loop over distinct galaxies (tiny catalogs only)."""
+    xq, yq, g1, g2, w, _ = _cat(cat)
+    th = _c(np.asarray(theta, dtype=np.float64).reshape(3), np.float64)
+    cen = _c(np.atleast_2d(np.asarray(centres, dtype=np.float64)), np.float64)
+    rcut = float(rcut_factor) * float(th.max())
+    out = np.zeros((cen.shape[0], 2), dtype=np.float64)
+    if brute:
+        for t in range(cen.shape[0]):
+            nu, de = C.c_double(), C.c_double()
+            _check(lib().orc_map3_direct_brute(cat.n, _p(xq), _p(yq), _p(g1), _p(g2), _p(w), float(cat.quantum),
+                                               float(cen[t, 0]), float(cen[t, 1]), _p(th), rcut,
+                                               C.byref(nu), C.byref(de)))
+            out[t] = (nu.value, de.value)
+    else:
+        _check(lib().orc_map3_direct(cat.n, _p(xq), _p(yq), _p(g1), _p(g2), _p(w), float(cat.quantum),
+                                     cen.shape[0], _p(cen), _p(th), rcut, _p(out)))
+    return out
 
 
 def num_threads() -> int:
@@ -290,4 +316,4 @@ def pipeline(s: Setup, cat, theta_ap, centres: Optional[np.ndarray] = None) -> R
 
 __all__ = ["Setup", "build_oracle", "edges", "moments", "count_pairs", "contract",
            "edge_correct", "degenerate_correction", "to_gamma", "to_map3", "filter_F", "cen_factor", "combine8", "brute",
-           "pipeline", "num_threads", "set_num_threads", "Result", "Brute"]
+           "pipeline", "num_threads", "set_num_threads", "map3_direct", "Result", "Brute"]
