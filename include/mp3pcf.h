@@ -166,6 +166,24 @@ mp3pcf_status mp3pcf_to_gamma(mp3pcf_ctx* ctx, const double* d_gamma_n, int32_t 
 mp3pcf_status mp3pcf_to_map3(mp3pcf_ctx* ctx, const double* d_gamma_cen, int64_t n_ap,
                              const double* d_theta_ap, double* d_corr, double* d_m8);
 
+/* ---- Direct estimator of the third-order aperture mass (Sec. 5.3, Eq. MapDirectEstimator), an
+ * estimate of <M_ap^3> independent of the 3PCF route, for unmasked catalogs. For every aperture
+ * centre t (d_centres [n_centres][2] double, arcmin, in the frame of the fixed-point positions:
+ * x = xq * quantum) and every radii triple a (d_theta_ap [n_ap][3] double, arcmin, > 0), writes
+ * d_out[t][a][0] = sum over distinct galaxies i, j, k of w_i w_j w_k Q_1(r_i) Q_2(r_j) Q_3(r_k)
+ * gt_i gt_j gt_k and d_out[t][a][1] = the same sum without the tangential shears gt (about the
+ * centre), Q the filter of Eq. CrittendenQ; the estimate at the centre is their ratio and
+ * <M_ap^3> is its average over apertures. Galaxies farther than rcut_factor * max(theta) from a
+ * centre are left out (the paper uses 4). The catalog is the caller's device SoA (as in
+ * mp3pcf_accumulate_moments, unsorted; zbin is not used); quantum comes from the context's
+ * configuration. Sums in FP64 in the order of a fixed block reduction. Stream-ordered on the
+ * context's stream. Returns EINVAL for bad arguments (negative counts, NULL pointers with
+ * non-zero counts, rcut_factor <= 0, more than 2^31 - 1 apertures x triples). */
+mp3pcf_status mp3pcf_map3_direct(mp3pcf_ctx* ctx, int64_t n, const int32_t* d_xq, const int32_t* d_yq,
+                                 const float* d_g1, const float* d_g2, const float* d_w, int64_t n_centres,
+                                 const double* d_centres, int64_t n_ap, const double* d_theta_ap,
+                                 double rcut_factor, double* d_out);
+
 /* ---- Failure injection, for tests of failure detection (host side only; nothing faults or
  * traps the GPU). MP3PCF_INJECT_WAIT_TIMEOUT: the tensor-core contraction issues no TMA copies,
  * so its bounded mbarrier waits (about a second each) run out; every role aborts, frees its

@@ -235,6 +235,27 @@ class Estimator:
         native.check(native.lib().mp3pcf_graph_stats(self._ctx, C.byref(a), C.byref(b)), "mp3pcf_graph_stats")
         return int(a.value), int(b.value)
 
+    # ------------------------------------------------------------------ direct estimator
+    def map3_direct(self, xq, yq, g1, g2, w, theta_ap, centres, rcut_factor=4.0):
+        """Numerator and denominator [n_centres][n_ap][2] (float64) of the direct estimator of
+        <M_ap^3> (Sec. 5.3, Eq. MapDirectEstimator) at the aperture centres [n_centres][2]
+        (arcmin, x = xq * quantum) for the radii triples theta_ap [n_ap][3] (arcmin); galaxies
+        beyond rcut_factor * max(theta) from a centre are left out."""
+        torch = _torch()
+        n = int(xq.numel())
+        for t, dt, nm in ((xq, torch.int32, "xq"), (yq, torch.int32, "yq"), (g1, torch.float32, "g1"),
+                          (g2, torch.float32, "g2"), (w, torch.float32, "w")):
+            _need(t, dt, nm, n)
+        th = torch.as_tensor(np.atleast_2d(np.asarray(theta_ap, dtype=np.float64)),
+                             device=self.device).contiguous()
+        cen = torch.as_tensor(np.asarray(centres, dtype=np.float64).reshape(-1, 2), device=self.device).contiguous()
+        out = torch.empty((cen.shape[0], th.shape[0], 2), dtype=torch.float64, device=self.device)
+        native.check(native.lib().mp3pcf_map3_direct(self._ctx, n, _ptr(xq), _ptr(yq), _ptr(g1), _ptr(g2), _ptr(w),
+                                                     cen.shape[0], _ptr(cen), th.shape[0], _ptr(th),
+                                                     float(rcut_factor), _ptr(out)),
+                     "mp3pcf_map3_direct", self._ctx)
+        return out
+
     # ------------------------------------------------------------------ adjoints
     def to_map3_adjoint(self, theta_ap, grad_m8=None, grad_corr=None):
         """dL/dGamma^cen from dL/dm8 and/or dL/dcorr (complex gradients: dL/dRe + i dL/dIm)."""
@@ -310,6 +331,32 @@ class Estimator:
         gc = self.to_gamma(gam, 1)
         corr, m8 = self.to_map3(gc, theta_ap)
         return Measurement(ups, norm, gam, ns, gx, gc, corr, m8)
+
+
+def aperture_centres(xq, yq, quantum, theta_ap, spacing=None, rcut_factor=4.0):
+    """Aperture centres [n][2] (arcmin) on a square grid over the catalog's bounding box, at
+    least rcut_factor * max(theta) from its edges (the direct estimator's apertures must lie
+    inside the field, Sec. 5.3); the grid spacing defaults to the smallest radius."""
+    x = np.asarray(xq.cpu() if hasattr(xq, "cpu") else xq, dtype=np.float64) * quantum
+    y = np.asarray(yq.cpu() if hasattr(yq, "cpu") else yq, dtype=np.float64) * quantum
+    th = np.asarray(theta_ap, dtype=np.float64)
+    margin = float(rcut_factor) * float(th.max())
+    step = float(spacing) if spacing else float(th.min())
+    gx = np.arange(x.min() + margin, x.max() - margin + 1e-9, step)
+    gy = np.arange(y.min() + margin, y.max() - margin + 1e-9, step)
+    if gx.size == 0 or gy.size == 0:
+        return np.zeros((0, 2))
+    X, Y = np.meshgrid(gx, gy, indexing="ij")
+    return np.stack([X.ravel(), Y.ravel()], axis=1)
+
+
+def map3_from_direct(out):
+    """<M_ap^3> per radii triple from mp3pcf_map3_direct's output: the mean over the apertures
+    of numerator / denominator (apertures with a zero denominator left out)."""
+    o = out.double().cpu().numpy() if hasattr(out, "cpu") else np.asarray(out, dtype=np.float64)
+    num, den = o[..., 0], o[..., 1]
+    ok = den != 0
+    return np.array([(num[ok[:, a], a] / den[ok[:, a], a]).mean() for a in range(o.shape[1])])
 
 
 def catalog_to_device(cat, device=None):

@@ -921,6 +921,27 @@ mp3pcf_status mp3pcf_to_map3(mp3pcf_ctx* ctx, const double* d_gamma_cen, int64_t
     return MP3PCF_OK;
 }
 
+// ------------------------------------------------------------------ direct estimator of <M_ap^3>
+
+mp3pcf_status mp3pcf_map3_direct(mp3pcf_ctx* ctx, int64_t n, const int32_t* d_xq, const int32_t* d_yq,
+                                 const float* d_g1, const float* d_g2, const float* d_w, int64_t n_centres,
+                                 const double* d_centres, int64_t n_ap, const double* d_theta_ap,
+                                 double rcut_factor, double* d_out)
+{
+    if (!ctx) return MP3PCF_EINVAL;
+    if (n < 0 || n_centres < 0 || n_ap < 0 || !(rcut_factor > 0.0) ||
+        (n > 0 && (!d_xq || !d_yq || !d_g1 || !d_g2 || !d_w)) ||
+        (n_centres > 0 && n_ap > 0 && (!d_centres || !d_theta_ap || !d_out)) ||
+        n_centres * n_ap > 0x7fffffffLL)
+        return fail(ctx, MP3PCF_EINVAL, "bad argument");
+    ctx->err.clear();
+    if (n_centres == 0 || n_ap == 0) return MP3PCF_OK;
+    NvtxRange nvtx("mp3pcf map3_direct");
+    MP3_CK(launch_map3_direct(n, d_xq, d_yq, d_g1, d_g2, d_w, ctx->cfg.quantum, n_centres, d_centres, (int)n_ap,
+                              d_theta_ap, rcut_factor, d_out, ctx->st));
+    return MP3PCF_OK;
+}
+
 // ------------------------------------------------------------------ failure injection
 
 mp3pcf_status mp3pcf_inject(mp3pcf_ctx* ctx, int32_t what, int32_t on)

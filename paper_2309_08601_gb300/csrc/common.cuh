@@ -139,6 +139,10 @@ cudaError_t launch_edge_correct(const PostArgs& p, const double* ups, const doub
                                 double* gam, unsigned long long* n_singular, cudaStream_t st);
 cudaError_t launch_to_gamma(const PostArgs& p, const double* gam, int projection, double* out,
                             cudaStream_t st);
+// direct estimator of <M_ap^3> (Sec. 5.3): out[centre][radii triple][2] = (numerator, denominator)
+cudaError_t launch_map3_direct(int64_t n, const int32_t* xq, const int32_t* yq, const float* g1, const float* g2,
+                               const float* w, double quantum, int64_t n_cen, const double* centres, int n_ap,
+                               const double* theta, double rcut_factor, double* out, cudaStream_t st);
 cudaError_t launch_to_map3(const PostArgs& p, const double* gcen, int n_ap, const double* theta,
                            double* partial, int chunks, double* corr, double* m8,
                            cudaStream_t st);
