@@ -8,7 +8,7 @@
  * it. It shares no code with the CUDA library: it has its own configuration struct, its own
  * bin-edge table, its own neighbour search and its own arithmetic, all written from the paper.
  *
- * Conventions (readings of the paper where it is silent; each is listed in the design doc):
+ * Conventions (readings of the paper where it is silent):
  *  - shear gamma_c = gamma_1 + i gamma_2; projected shear gamma(X; zeta) = -gamma_c e^{-2 i zeta}
  *    (Sec. 2.1, Eq. gammatx_def);
  *  - moments use e^{+i n phi} exactly as Eq. Gn_disc;
