@@ -166,6 +166,27 @@ mp3pcf_status mp3pcf_to_gamma(mp3pcf_ctx* ctx, const double* d_gamma_n, int32_t 
 mp3pcf_status mp3pcf_to_map3(mp3pcf_ctx* ctx, const double* d_gamma_cen, int64_t n_ap,
                              const double* d_theta_ap, double* d_corr, double* d_m8);
 
+/* ---- Grid-based approximation (Sec. 3.2): the pixel catalog of a regular grid. Pixel (ix, iy)
+ * of z-bin z covers [origin[0] + ix * pixel_q, origin[0] + (ix + 1) * pixel_q) x (the same in y),
+ * in fixed-point quanta; galaxies outside the grid count in its edge pixels. Each non-empty pixel
+ * becomes a galaxy at its centre (origin + i * pixel_q + pixel_q / 2) with weight W = sum of w and
+ * shear (sum of w gamma) / W, written in (z, iy, ix) order to the caller's device arrays d_pxq,
+ * d_pyq (int32), d_pg1, d_pg2, d_pw (float) and d_pzbin (uint8; required when n_z > 1, else may be
+ * NULL), each with room for n_z * npy * npx entries; *h_count receives the number of non-empty
+ * pixels (the call synchronises the context's stream for it). The catalog d_xq..d_w, d_zbin is
+ * the caller's device SoA as in mp3pcf_accumulate_moments. The sums are taken in FP64 (exact for
+ * the products and their sums, so independent of the order of the additions). The pixel catalog
+ * is an ordinary catalog for mp3pcf_accumulate_moments and the rest of the path: its moments are
+ * the grid moments G_n^Delta, W_n^Delta and its contraction is Eq. UpsilonmuGrid (the outer sum
+ * over pixels). Returns EINVAL for bad arguments (pixel_q < 1,
+ * npx or npy < 1, more than 2^31 - 1 pixels, NULL pointers), ENOMEM if the context's scratch
+ * cannot grow. */
+mp3pcf_status mp3pcf_grid_catalog(mp3pcf_ctx* ctx, int64_t n, const int32_t* d_xq, const int32_t* d_yq,
+                                  const float* d_g1, const float* d_g2, const float* d_w, const uint8_t* d_zbin,
+                                  const int64_t* h_origin, int64_t pixel_q, int32_t npx, int32_t npy,
+                                  int32_t* d_pxq, int32_t* d_pyq, float* d_pg1, float* d_pg2, float* d_pw,
+                                  uint8_t* d_pzbin, int64_t* h_count);
+
 /* ---- Direct estimator of the third-order aperture mass (Sec. 5.3, Eq. MapDirectEstimator), an
  * estimate of <M_ap^3> independent of the 3PCF route, for unmasked catalogs. For every aperture
  * centre t (d_centres [n_centres][2] double, arcmin, in the frame of the fixed-point positions:

@@ -129,9 +129,9 @@ def grid_catalog(cat, origin, pixel_q: int, npx: int, npy: int, n_z: int = 1):
     """The pixel catalog of the grid-based approximation (Sec. 3.2): the weights w and the
     products w gamma of the galaxies summed per pixel of side pixel_q quanta (pixel (ix, iy) of
     z-bin z covers [origin + i pixel_q, origin + (i + 1) pixel_q) on each axis); each pixel becomes
-    a galaxy at its centre with weight W = sum w and shear (sum w gamma) / W (0 for an empty
-    pixel). Dense output over all npx x npy x n_z pixels, in (z, iy, ix) order. The sums are taken
-    in FP64, where the products of two float32 numbers and their sums over a pixel are exact."""
+    a galaxy at its centre with weight W = sum w and shear (sum w gamma) / W; the non-empty pixels
+    in (z, iy, ix) order. The sums are taken in FP64, where the products of two float32 numbers
+    and their sums over a pixel are exact."""
     x0, y0 = int(origin[0]), int(origin[1])
     ix = np.clip((np.asarray(cat.xq, np.int64) - x0) // pixel_q, 0, npx - 1)
     iy = np.clip((np.asarray(cat.yq, np.int64) - y0) // pixel_q, 0, npy - 1)
@@ -145,14 +145,12 @@ def grid_catalog(cat, origin, pixel_q: int, npx: int, npy: int, n_z: int = 1):
     np.add.at(W, p, w)
     np.add.at(A, p, w * np.asarray(cat.g1, np.float64))
     np.add.at(B, p, w * np.asarray(cat.g2, np.float64))
-    safe = np.where(W > 0, W, 1.0)
-    k = np.arange(npix)
+    k = np.nonzero(W > 0)[0]
     pix_x = x0 + (k % npx) * pixel_q + pixel_q // 2
     pix_y = y0 + ((k // npx) % npy) * pixel_q + pixel_q // 2
     from paper_2309_08601_gb300.synth import Catalog
-    return Catalog(pix_x.astype(np.int32), pix_y.astype(np.int32),
-                   np.where(W > 0, A / safe, 0.0).astype(np.float32),
-                   np.where(W > 0, B / safe, 0.0).astype(np.float32), W.astype(np.float32),
+    return Catalog(pix_x.astype(np.int32), pix_y.astype(np.int32), (A[k] / W[k]).astype(np.float32),
+                   (B[k] / W[k]).astype(np.float32), W[k].astype(np.float32),
                    None if n_z == 1 else (k // (npx * npy)).astype(np.uint8), 0.0, cat.quantum)
 
 

@@ -235,6 +235,42 @@ class Estimator:
         native.check(native.lib().mp3pcf_graph_stats(self._ctx, C.byref(a), C.byref(b)), "mp3pcf_graph_stats")
         return int(a.value), int(b.value)
 
+    # ------------------------------------------------------------------ grid-based approximation
+    def grid_catalog(self, xq, yq, g1, g2, w, zbin=None, pixel_arcmin=1.0, origin=None, shape=None):
+        """The pixel catalog of the grid-based approximation (Sec. 3.2) through mp3pcf_grid_catalog:
+        device tensors (xq, yq, g1, g2, w, zbin-or-None) of the non-empty pixels, in (z, iy, ix)
+        order, of side pixel_arcmin (rounded to whole quanta); origin (quanta) and shape (npx, npy) default to
+        the catalog's bounding box. Its moments and multipoles (measure, accumulate_moments, ...)
+        are the grid estimator's (Eq. UpsilonmuGrid)."""
+        torch = _torch()
+        n = int(xq.numel())
+        for t, dt, nm in ((xq, torch.int32, "xq"), (yq, torch.int32, "yq"), (g1, torch.float32, "g1"),
+                          (g2, torch.float32, "g2"), (w, torch.float32, "w")):
+            _need(t, dt, nm, n)
+        _need(zbin, torch.uint8, "zbin", n)
+        pq = max(1, int(round(float(pixel_arcmin) / float(self.cfg.quantum))))
+        if origin is None:
+            origin = (int(xq.min()), int(yq.min())) if n else (0, 0)
+        if shape is None:
+            npx = (int(xq.max()) - int(origin[0])) // pq + 1 if n else 1
+            npy = (int(yq.max()) - int(origin[1])) // pq + 1 if n else 1
+        else:
+            npx, npy = int(shape[0]), int(shape[1])
+        nz = int(self.cfg.n_z)
+        m = nz * npx * npy
+        out = (torch.empty(m, dtype=torch.int32, device=self.device), torch.empty(m, dtype=torch.int32, device=self.device),
+               torch.empty(m, dtype=torch.float32, device=self.device), torch.empty(m, dtype=torch.float32, device=self.device),
+               torch.empty(m, dtype=torch.float32, device=self.device),
+               torch.empty(m, dtype=torch.uint8, device=self.device) if nz > 1 else None)
+        org = (C.c_int64 * 2)(int(origin[0]), int(origin[1]))
+        cnt = C.c_int64()
+        native.check(native.lib().mp3pcf_grid_catalog(self._ctx, n, _ptr(xq), _ptr(yq), _ptr(g1), _ptr(g2), _ptr(w),
+                                                      _ptr(zbin), org, pq, npx, npy, *[_ptr(t) for t in out],
+                                                      C.byref(cnt)),
+                     "mp3pcf_grid_catalog", self._ctx)
+        k = int(cnt.value)
+        return tuple(None if t is None else t[:k] for t in out)
+
     # ------------------------------------------------------------------ direct estimator
     def map3_direct(self, xq, yq, g1, g2, w, theta_ap, centres, rcut_factor=4.0):
         """Numerator and denominator [n_centres][n_ap][2] (float64) of the direct estimator of

@@ -375,6 +375,8 @@ struct mp3pcf_ctx {
     DevBuf gG, gW, gv, gtab, adjscratch;  // adjoint workspace
     DevBuf degen;                       // exclude_degenerate sums per (centre, z, bin)
     DevBuf zrange;                      // [nz + 1] centre range of each z-bin
+    DevBuf gridsum;                     // per-pixel FP64 sums of the grid-based approximation
+    DevBuf gridflag;                    // its non-empty flags and their exclusive scan
     // tracing: per-stage event pairs and kernel-launch counts
     bool timing = false;
     int64_t launches[6] = {0, 0, 0, 0, 0, 0};
@@ -553,7 +555,8 @@ mp3pcf_status mp3pcf_destroy(mp3pcf_ctx* ctx)
                       &ctx->crank, &ctx->oflag, &ctx->orank, &ctx->centre_idx, &ctx->crow,
                       &ctx->G, &ctx->W, &ctx->pairs, &ctx->partial, &ctx->singular,
                       &ctx->m3partial, &ctx->ccoef, &ctx->gG, &ctx->gW, &ctx->gv, &ctx->gtab,
-                      &ctx->adjscratch, &ctx->degen, &ctx->bups, &ctx->bnorm, &ctx->bgam, &ctx->bgcen, &ctx->berr};
+                      &ctx->adjscratch, &ctx->degen, &ctx->zrange, &ctx->gridsum, &ctx->gridflag, &ctx->bups, &ctx->bnorm,
+                      &ctx->bgam, &ctx->bgcen, &ctx->berr};
     for (DevBuf* b : bufs) b->release();
     if (ctx->batch_st) cudaStreamDestroy(ctx->batch_st);
     for (cudaEvent_t ev : ctx->batch_ev)
@@ -918,6 +921,43 @@ mp3pcf_status mp3pcf_to_map3(mp3pcf_ctx* ctx, const double* d_gamma_cen, int64_t
     ctx->launches[ST_MAP3] += 2;
     MP3_CK(launch_to_map3(post_args(ctx), d_gamma_cen, (int)n_ap, d_theta_ap,
                           ctx->m3partial.as<double>(), chunks, d_corr, d_m8, ctx->st));
+    return MP3PCF_OK;
+}
+
+// ------------------------------------------------------------------ grid-based approximation
+
+mp3pcf_status mp3pcf_grid_catalog(mp3pcf_ctx* ctx, int64_t n, const int32_t* d_xq, const int32_t* d_yq,
+                                  const float* d_g1, const float* d_g2, const float* d_w, const uint8_t* d_zbin,
+                                  const int64_t* h_origin, int64_t pixel_q, int32_t npx, int32_t npy,
+                                  int32_t* d_pxq, int32_t* d_pyq, float* d_pg1, float* d_pg2, float* d_pw,
+                                  uint8_t* d_pzbin, int64_t* h_count)
+{
+    if (!ctx) return MP3PCF_EINVAL;
+    const int nz = ctx->cfg.n_z;
+    const int64_t npix = (int64_t)nz * npx * npy;
+    if (n < 0 || !h_origin || pixel_q < 1 || npx < 1 || npy < 1 || npix > 0x7fffffffLL ||
+        (n > 0 && (!d_xq || !d_yq || !d_g1 || !d_g2 || !d_w)) || !d_pxq || !d_pyq || !d_pg1 || !d_pg2 ||
+        !d_pw || (nz > 1 && !d_pzbin) || !h_count)
+        return fail(ctx, MP3PCF_EINVAL, "bad argument");
+    // pixel centres must stay within the int32 fixed-point range
+    const long long xmax = h_origin[0] + (long long)npx * pixel_q, ymax = h_origin[1] + (long long)npy * pixel_q;
+    if (h_origin[0] < INT_MIN || h_origin[1] < INT_MIN || xmax > INT_MAX || ymax > INT_MAX)
+        return fail(ctx, MP3PCF_EINVAL, "grid outside the fixed-point range");
+    ctx->err.clear();
+    MP3_CK(ctx->gridsum.ensure(sizeof(double) * 3 * (size_t)npix));
+    MP3_CK(ctx->gridflag.ensure(sizeof(int) * 2 * ((size_t)npix + 1)));
+    NvtxRange nvtx("mp3pcf grid_catalog");
+    int* flags = ctx->gridflag.as<int>();
+    int* rank = flags + npix + 1;
+    MP3_CK(launch_grid_sums(n, d_xq, d_yq, d_g1, d_g2, d_w, d_zbin, nz, h_origin[0], h_origin[1], pixel_q, npx, npy,
+                            ctx->gridsum.as<double>(), flags, ctx->n_sm, ctx->st));
+    if (mp3pcf_status s = scan_exclusive(ctx, flags, rank, npix)) return s;
+    MP3_CK(launch_grid_emit(nz, npx, npy, h_origin[0], h_origin[1], pixel_q, ctx->gridsum.as<double>(), rank, d_pxq,
+                            d_pyq, d_pg1, d_pg2, d_pw, nz > 1 ? d_pzbin : nullptr, ctx->n_sm, ctx->st));
+    int cnt = 0;
+    MP3_CK(cudaMemcpyAsync(&cnt, rank + npix, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    MP3_CK(cudaStreamSynchronize(ctx->st));
+    *h_count = cnt;
     return MP3PCF_OK;
 }
 

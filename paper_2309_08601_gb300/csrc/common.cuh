@@ -139,6 +139,14 @@ cudaError_t launch_edge_correct(const PostArgs& p, const double* ups, const doub
                                 double* gam, unsigned long long* n_singular, cudaStream_t st);
 cudaError_t launch_to_gamma(const PostArgs& p, const double* gam, int projection, double* out,
                             cudaStream_t st);
+// pixel catalog of the grid-based approximation (Sec. 3.2): per-pixel sums (scratch: 3 n_z npx npy
+// doubles) and non-empty flags, then, with rank = exclusive scan of the flags, the compacted pixels
+cudaError_t launch_grid_sums(int64_t n, const int32_t* xq, const int32_t* yq, const float* g1, const float* g2,
+                             const float* w, const uint8_t* zb, int nz, long long x0, long long y0, long long pq,
+                             int npx, int npy, double* scratch, int* flags, int n_sm, cudaStream_t st);
+cudaError_t launch_grid_emit(int nz, int npx, int npy, long long x0, long long y0, long long pq, const double* scratch,
+                             const int* rank, int32_t* oxq, int32_t* oyq, float* og1, float* og2, float* ow,
+                             uint8_t* ozb, int n_sm, cudaStream_t st);
 // direct estimator of <M_ap^3> (Sec. 5.3): out[centre][radii triple][2] = (numerator, denominator)
 cudaError_t launch_map3_direct(int64_t n, const int32_t* xq, const int32_t* yq, const float* g1, const float* g2,
                                const float* w, double quantum, int64_t n_cen, const double* centres, int n_ap,
