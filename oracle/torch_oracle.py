@@ -204,12 +204,58 @@ class Map3Oracle:
             Ws.append(W)
         return torch.cat(Gs), torch.cat(Ws)
 
+    def degenerate(self, v, w):
+        """With s.exclude_degenerate: the j = k triplets' share of (ups, norm), to be removed. For
+        a centre i and its neighbours k of z-bin z in bin b (u = e^{-i phi_ik}): D6 = sum v_k^2
+        u^6, D2 = sum v_k^2 u^2, E2 = sum |v_k|^2 u^2, F = sum w_k^2; on b1 = b2 = b of the
+        triplet (Z1, z, z) every order of Upsilon_0 holds -sum_i v_i D6, Upsilon_1 -sum_i v_i^*
+        D2, Upsilon_2 and Upsilon_3 -sum_i v_i E2, and N holds sum_i w_i F (Eqs. TripletUpsilon,
+        TripletNorm with j = k). Returns (d_ups, d_norm) in the layouts of contract."""
+        s = self.s
+        nb, nz, nmax = s.n_bins, s.n_z, s.n_max
+        pr = self.pairs
+        i = torch.as_tensor(pr.i)
+        k = torch.as_tensor(pr.k)
+        b = torch.as_tensor(pr.b)
+        z = torch.as_tensor(self.zb[pr.k])
+        u = torch.polar(torch.ones(len(pr.phi), dtype=torch.float64), -torch.as_tensor(pr.phi))
+        u2 = u * u
+        vk, wk = v[k], w[k]
+        nc = len(self.centres)
+        row = (i * nz + z) * nb + b
+        D6 = torch.zeros(nc * nz * nb, dtype=torch.complex128).index_add(0, row, vk * vk * u2 * u2 * u2)
+        D2 = torch.zeros(nc * nz * nb, dtype=torch.complex128).index_add(0, row, vk * vk * u2)
+        E2 = torch.zeros(nc * nz * nb, dtype=torch.complex128).index_add(0, row, (vk * vk.conj()) * u2)
+        F = torch.zeros(nc * nz * nb, dtype=torch.float64).index_add(0, row, wk * wk)
+        cidx = torch.as_tensor(self.centres)
+        vc, wc = v[cidx], w[cidx]
+        zc = self.zb[self.centres]
+        d_ups = torch.zeros((nz ** 3, 4, nmax + 1, nb, nb), dtype=torch.complex128)
+        d_norm = torch.zeros((nz ** 3, 2 * nmax + 1, nb, nb), dtype=torch.complex128)
+        D6, D2, E2, F = (t.reshape(nc, nz, nb) for t in (D6, D2, E2, F))
+        bb = torch.arange(nb)
+        for z1 in range(nz):
+            sel = torch.as_tensor(zc == z1)
+            for zz in range(nz):
+                zt = (z1 * nz + zz) * nz + zz
+                s0 = torch.einsum("c,cb->b", vc[sel], D6[sel, zz])
+                s1 = torch.einsum("c,cb->b", vc[sel].conj(), D2[sel, zz])
+                s2 = torch.einsum("c,cb->b", vc[sel], E2[sel, zz])
+                sn = torch.einsum("c,cb->b", wc[sel], F[sel, zz]).to(torch.complex128)
+                for mu, sm in ((0, s0), (1, s1), (2, s2), (3, s2)):
+                    d_ups[zt, mu, :, bb, bb] = -sm[None, :].expand(nmax + 1, nb)
+                d_norm[zt, :, bb, bb] = sn[None, :].expand(2 * nmax + 1, nb)
+        return d_ups, d_norm
+
     def downstream(self, G, W, v, w):
         """Everything after the moments: (ups, norm, gamma_n, gamma_cen, corr, m8)."""
         s = self.s
         cidx = torch.as_tensor(self.centres)
         zc = torch.as_tensor(self.zb[self.centres])
         ups, norm = contract(s, G, W, v[cidx], w[cidx], zc)
+        if getattr(s, "exclude_degenerate", 0):
+            d_ups, d_norm = self.degenerate(v, w)
+            ups, norm = ups - d_ups, norm - d_norm
         gam = edge_correct(s, ups, norm)                         # [z3][4][D][nb][nb]
         gx = torch.einsum("zmnbc,nk->zmbck", gam, self.ephi)     # Gamma^x(phi_k)
         gc = gx * self.cen[None]                                 # centroid projection

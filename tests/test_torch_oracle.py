@@ -68,3 +68,20 @@ def test_gradient_against_central_differences(small_case):
             args_m[which][k] -= h
             fd = (L(*args_p) - L(*args_m)) / (2 * h)
             assert abs(fd - float(grad[k])) <= 1e-6 * max(abs(fd), float(grad.abs().max())), (k, which)
+
+
+@pytest.mark.parametrize("n_z", [1, 2])
+def test_forward_excluding_degenerate_triplets_equals_c_oracle(orc, n_z):
+    """exclude_degenerate (j = k left out) in the differentiable restatement against the C oracle,
+    whose correction is pinned against the brute force without j = k."""
+    from oracle import torch_oracle as to
+    rng = np.random.default_rng(8 + n_z)
+    n = 250
+    cat = hand_catalog(rng.uniform(0, 14, (n, 2)), rng.normal(0, .3, n) + 1j * rng.normal(0, .3, n),
+                       rng.uniform(0.5, 1.5, n), rng.integers(0, n_z, n) if n_z > 1 else None)
+    s = orc.Setup(**S_SMALL, n_z=n_z, exclude_degenerate=1)
+    r = orc.pipeline(s, cat, TH)
+    mo = to.Map3Oracle(s, cat, TH, chunk_pairs=20_000)
+    ups, norm, gam, gc, corr, m8 = [x.detach().numpy() for x in mo.forward(_t(cat.g1), _t(cat.g2), _t(cat.w))]
+    for a, b in ((ups, r.ups), (norm, r.norm), (gam, r.gamma_n), (m8, r.m8)):
+        assert rel_err(a, b) < 1e-11
