@@ -284,9 +284,9 @@ mp3pcf_status mp3pcf_edge_correct_adjoint(mp3pcf_ctx* ctx, const double* d_norm,
  * LAST accumulate call (the context still holds its sorted copy and moments): ADDS dL/dgamma_1,
  * dL/dgamma_2 and dL/dw per galaxy, in the caller's order, to d_grad_g1, d_grad_g2, d_grad_w
  * (float [n]; any may be NULL) given dL/dUpsilon and dL/dN. n and d_g1, d_g2, d_w must be the
- * catalog of that call (EINVAL if n differs; EUNSUPPORTED with exclude_degenerate). Arithmetic in
- * the forward moment precision; the
- * scatter to neighbours uses atomics, so the result is not bit-reproducible. */
+ * catalog of that call (EINVAL if n differs). With exclude_degenerate the gradient of the
+ * removed j = k terms is included. Arithmetic in the forward moment precision; the scatter to
+ * neighbours uses atomics, so the result is not bit-reproducible. */
 mp3pcf_status mp3pcf_moments_adjoint(mp3pcf_ctx* ctx, const double* d_grad_upsilon, const double* d_grad_norm,
                                      int64_t n, const float* d_g1, const float* d_g2, const float* d_w,
                                      float* d_grad_g1, float* d_grad_g2, float* d_grad_w);

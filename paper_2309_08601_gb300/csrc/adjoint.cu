@@ -493,40 +493,6 @@ __global__ void adjoint_finish(int64_t n, const int* __restrict__ perm, const T*
     }
 }
 
-template <typename T>
-static cudaError_t run(const AdjArgs<T>& a, int64_t n, const int* perm, const float* g1, const float* g2,
-                       const float* w, float* dg1, float* dg2, float* dw, int n_sm, cudaStream_t st)
-{
-    cudaError_t e = cudaMemsetAsync(a.gvw, 0, sizeof(T) * 4 * (size_t)n, st);
-    if (e != cudaSuccess) return e;
-    if (a.n_centres > 0) {
-        const int MG = 2 * a.n_max + 3, MW = 2 * a.n_max + 1;
-        dim3 g1d((a.n_centres + kTileC - 1) / kTileC, MG + MW);
-        const int64_t z3 = (int64_t)a.nz * a.nz * a.nz, nbb = (int64_t)a.nb * a.nb;
-        const int64_t nU = z3 * 4 * (a.n_max + 1), tot = (nU + z3 * (2 * a.n_max + 1)) * nbb;
-        grad_tables<T><<<(unsigned)std::min<int64_t>((tot + 255) / 256, (int64_t)n_sm * 16), 256, 0, st>>>(a, nU, tot);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        contract_adjoint_moments<T><<<g1d, 256, 0, st>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        const size_t sm_coef = sizeof(cx<T>) * (size_t)a.nb * a.nb;
-        e = set_smem_attr(contract_adjoint_coef<T>, sm_coef);
-        if (e != cudaSuccess) return e;
-        constexpr int per_block = kCoefWarps * kCoefCentres;
-        contract_adjoint_coef<T><<<(a.n_centres + per_block - 1) / per_block, kCoefWarps * 32, sm_coef, st>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        const size_t sm_pair = sizeof(cx<T>) * (size_t)kPairWarps * (a.nz * (MG + MW) + kQueue) +
-                               sizeof(int) * (size_t)kPairWarps * kQueue;
-        e = set_smem_attr(moments_adjoint_pairs<T>, sm_pair);
-        if (e != cudaSuccess) return e;
-        const int blocks = (int)std::min<int64_t>((a.n_centres + kPairWarps - 1) / kPairWarps, (int64_t)n_sm * 32);
-        moments_adjoint_pairs<T><<<blocks, kPairWarps * 32, sm_pair, st>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)n_sm * 16));
-    adjoint_finish<T><<<gb, 256, 0, st>>>(n, perm, a.gvw, g1, g2, w, dg1, dg2, dw);
-    return cudaGetLastError();
-}
-
 // ------------------------------------------------------------------ exclude_degenerate
 
 template <typename T>
@@ -628,6 +594,100 @@ __global__ void __launch_bounds__(256) degenerate_correct(const AdjArgs<T> a, co
     }
 }
 
+// ---- adjoint of the exclude_degenerate correction. The forward adds S0 = sum_i v_i D6_i to every
+// order of Upsilon_0, S1 = sum_i v_i^* D2_i to Upsilon_1, S2 = sum_i v_i E2_i to Upsilon_2 and
+// Upsilon_3 and subtracts SN = sum_i w_i F_i from Re N (b1 = b2, Z2 = Z3). Block-free pass first:
+// per (Z1, z, bin) gS0 = sum_n dL/dUpsilon_0,n, gS1, gS2 (Upsilon_2 and _3) and gSN = -sum_m
+// Re dL/dN_m, stored as dgs[(z1 nz + z) nb + b][0..3] (gSN in the real part).
+__global__ void degenerate_grad_sums(int nz, int nb, int n_max, const double* __restrict__ gups,
+                                     const double* __restrict__ gnorm, cx<double>* __restrict__ dgs)
+{
+    const int NN = n_max + 1, NW = 2 * n_max + 1;
+    const int total = nz * nz * nb;
+    const size_t nbb = (size_t)nb * nb;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int b = t % nb, z = (t / nb) % nz, z1 = t / (nb * nz);
+        const int zt = (z1 * nz + z) * nz + z;
+        const size_t bb = (size_t)b * nb + b;
+        cx<double> g[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+        for (int n = 0; n < NN; ++n)
+            for (int mu = 0; mu < 4; ++mu) {
+                const size_t i = 2 * ((((size_t)zt * 4 + mu) * NN + n) * nbb + bb);
+                const int slot = mu < 3 ? mu : 2;
+                g[slot].x += gups[i];
+                g[slot].y += gups[i + 1];
+            }
+        double gn = 0.0;
+        for (int m = 0; m < NW; ++m) gn -= gnorm[2 * (((size_t)zt * NW + m) * nbb + bb)];
+        dgs[(size_t)t * 4 + 0] = g[0];
+        dgs[(size_t)t * 4 + 1] = g[1];
+        dgs[(size_t)t * 4 + 2] = g[2];
+        dgs[(size_t)t * 4 + 3] = cx<double>{gn, 0.0};
+    }
+}
+
+// Warp per centre i: per (bin, z) of the neighbours, with u = e^{-i phi_ij},
+//   grad v_j += 2 v_j^* (u^6)^* gD6 + 2 v_j^* (u^2)^* gD2 + 2 v_j Re(gE2 (u^2)^*),
+//   grad w_j += 2 w_j gF,   gD6 = v_i^* gS0, gD2 = v_i gS1, gE2 = v_i^* gS2, gF = w_i gSN,
+// and, with the centre's own sums D6, D2, E2, F (re-formed in the same walk),
+//   grad v_i += D6^* gS0 + D2 gS1^* + E2^* gS2,   grad w_i += F gSN.
+template <typename T>
+__global__ void __launch_bounds__(kPairWarps * 32) degenerate_adjoint_pairs(const AdjArgs<T> a)
+{
+    const int nb = a.nb, nz = a.nz;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c = blockIdx.x * kPairWarps + warp; c < a.n_centres; c += gridDim.x * kPairWarps) {
+        const int d = a.centre_idx[c];
+        const int2 p = a.pos[d];
+        const int z1 = a.zs ? (int)a.zs[d] : 0;
+        const Pay<T> pv = a.pay[d];
+        const cx<double> vi{(double)pv.a, (double)pv.b};
+        const double wi = (double)pv.w;
+        double cgr = 0.0, cgi = 0.0, cgw = 0.0;  // the centre's own gradient (lane 0 adds it)
+        for (int b = 0; b < nb; ++b)
+            for (int z = 0; z < nz; ++z) {
+                const cx<double>* gs = a.dgs + ((size_t)(z1 * nz + z) * nb + b) * 4;
+                const cx<double> gS0 = gs[0], gS1 = gs[1], gS2 = gs[2];
+                const double gSN = gs[3].x;
+                const cx<double> gD6 = cmul(cconj(vi), gS0), gD2 = cmul(vi, gS1), gE2 = cmul(cconj(vi), gS2);
+                const double gF = wi * gSN;
+                double sd[7] = {0, 0, 0, 0, 0, 0, 0};  // this lane's share of D6, D2, E2, F
+                for_each_in_annulus(a.g, a.cell_start, a.pos, p.x, p.y, a.e2q[b], a.e2q[b + 1], z, lane,
+                                    [&](bool in, int k, long long dx, long long dy) {
+                    if (!in) return;
+                    const cx<T> zz = unit_dir<T>(dx, dy);
+                    const cx<double> u{(double)zz.x, -(double)zz.y};
+                    const cx<double> u2 = cmul(u, u), u6 = cmul(cmul(u2, u2), u2);
+                    const Pay<T> pk = a.pay[k];
+                    const cx<double> vj{(double)pk.a, (double)pk.b};
+                    const double wj = (double)pk.w;
+                    const cx<double> vj2 = cmul(vj, vj);
+                    const cx<double> d6 = cmul(vj2, u6), d2 = cmul(vj2, u2);
+                    const double vv = vj.x * vj.x + vj.y * vj.y;
+                    sd[0] += d6.x;
+                    sd[1] += d6.y;
+                    sd[2] += d2.x;
+                    sd[3] += d2.y;
+                    sd[4] += vv * u2.x;
+                    sd[5] += vv * u2.y;
+                    sd[6] += wj * wj;
+                    const cx<double> t6 = cmul(cmul(cconj(vj), cconj(u6)), gD6);
+                    const cx<double> t2 = cmul(cmul(cconj(vj), cconj(u2)), gD2);
+                    const double re = cmul(gE2, cconj(u2)).x;
+                    atomic_add_vw(a.gvw + 4 * (size_t)k, (T)(2.0 * (t6.x + t2.x + vj.x * re)),
+                                  (T)(2.0 * (t6.y + t2.y + vj.y * re)), (T)(2.0 * wj * gF));
+                });
+                for (int i = 0; i < 7; ++i) sd[i] = warp_sum(sd[i]);
+                const cx<double> D6{sd[0], sd[1]}, D2{sd[2], sd[3]}, E2{sd[4], sd[5]};
+                const cx<double> gv = cadd(cadd(cmul(cconj(D6), gS0), cmul(D2, cconj(gS1))), cmul(cconj(E2), gS2));
+                cgr += gv.x;
+                cgi += gv.y;
+                cgw += sd[6] * gSN;
+            }
+        if (lane == 0) atomic_add_vw(a.gvw + 4 * (size_t)d, (T)cgr, (T)cgi, (T)cgw);
+    }
+}
+
 template <typename T>
 static cudaError_t run_degenerate(const AdjArgs<T>& a, cx<T>* scratch, double* ups, double* norm, int n_sm,
                                   cudaStream_t st)
@@ -638,6 +698,49 @@ static cudaError_t run_degenerate(const AdjArgs<T>& a, cx<T>* scratch, double* u
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     degenerate_correct<T><<<a.nz * a.nz * a.nb, 256, 0, st>>>(a, scratch, ups, norm);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t run(const AdjArgs<T>& a, int64_t n, const int* perm, const float* g1, const float* g2,
+                       const float* w, float* dg1, float* dg2, float* dw, int n_sm, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(a.gvw, 0, sizeof(T) * 4 * (size_t)n, st);
+    if (e != cudaSuccess) return e;
+    if (a.n_centres > 0) {
+        const int MG = 2 * a.n_max + 3, MW = 2 * a.n_max + 1;
+        dim3 g1d((a.n_centres + kTileC - 1) / kTileC, MG + MW);
+        const int64_t z3 = (int64_t)a.nz * a.nz * a.nz, nbb = (int64_t)a.nb * a.nb;
+        const int64_t nU = z3 * 4 * (a.n_max + 1), tot = (nU + z3 * (2 * a.n_max + 1)) * nbb;
+        grad_tables<T><<<(unsigned)std::min<int64_t>((tot + 255) / 256, (int64_t)n_sm * 16), 256, 0, st>>>(a, nU, tot);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        contract_adjoint_moments<T><<<g1d, 256, 0, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const size_t sm_coef = sizeof(cx<T>) * (size_t)a.nb * a.nb;
+        e = set_smem_attr(contract_adjoint_coef<T>, sm_coef);
+        if (e != cudaSuccess) return e;
+        constexpr int per_block = kCoefWarps * kCoefCentres;
+        contract_adjoint_coef<T><<<(a.n_centres + per_block - 1) / per_block, kCoefWarps * 32, sm_coef, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const size_t sm_pair = sizeof(cx<T>) * (size_t)kPairWarps * (a.nz * (MG + MW) + kQueue) +
+                               sizeof(int) * (size_t)kPairWarps * kQueue;
+        e = set_smem_attr(moments_adjoint_pairs<T>, sm_pair);
+        if (e != cudaSuccess) return e;
+        const int blocks = (int)std::min<int64_t>((a.n_centres + kPairWarps - 1) / kPairWarps, (int64_t)n_sm * 32);
+        moments_adjoint_pairs<T><<<blocks, kPairWarps * 32, sm_pair, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (a.dgs && a.n_centres > 0) {
+        // the j = k triplets left out of the forward (exclude_degenerate)
+        const int total = a.nz * a.nz * a.nb;
+        degenerate_grad_sums<<<(total + 127) / 128, 128, 0, st>>>(a.nz, a.nb, a.n_max, a.gups, a.gnorm, a.dgs);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const int blocks = (int)std::min<int64_t>((a.n_centres + kPairWarps - 1) / kPairWarps, (int64_t)n_sm * 32);
+        degenerate_adjoint_pairs<T><<<blocks, kPairWarps * 32, 0, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)n_sm * 16));
+    adjoint_finish<T><<<gb, 256, 0, st>>>(n, perm, a.gvw, g1, g2, w, dg1, dg2, dw);
     return cudaGetLastError();
 }
 

@@ -374,6 +374,7 @@ struct mp3pcf_ctx {
     DevBuf G, W, pairs, partial, singular, m3partial, ccoef;
     DevBuf gG, gW, gv, gtab, adjscratch;  // adjoint workspace
     DevBuf degen;                       // exclude_degenerate sums per (centre, z, bin)
+    DevBuf degen_grad;                  // their gradient sums per (Z1, z, bin) in the adjoint
     DevBuf zrange;                      // [nz + 1] centre range of each z-bin
     DevBuf gridsum;                     // per-pixel FP64 sums of the grid-based approximation
     DevBuf gridflag;                    // its non-empty flags and their exclusive scan
@@ -555,7 +556,7 @@ mp3pcf_status mp3pcf_destroy(mp3pcf_ctx* ctx)
                       &ctx->crank, &ctx->oflag, &ctx->orank, &ctx->centre_idx, &ctx->crow,
                       &ctx->G, &ctx->W, &ctx->pairs, &ctx->partial, &ctx->singular,
                       &ctx->m3partial, &ctx->ccoef, &ctx->gG, &ctx->gW, &ctx->gv, &ctx->gtab,
-                      &ctx->adjscratch, &ctx->degen, &ctx->zrange, &ctx->gridsum, &ctx->gridflag, &ctx->bups, &ctx->bnorm,
+                      &ctx->adjscratch, &ctx->degen, &ctx->degen_grad, &ctx->zrange, &ctx->gridsum, &ctx->gridflag, &ctx->bups, &ctx->bnorm,
                       &ctx->bgam, &ctx->bgcen, &ctx->berr};
     for (DevBuf* b : bufs) b->release();
     if (ctx->batch_st) cudaStreamDestroy(ctx->batch_st);
@@ -1294,6 +1295,11 @@ static mp3pcf_status moments_adjoint_t(mp3pcf_ctx* ctx, const double* gups, cons
     a.gG = ctx->gG.as<cx<T>>();
     a.gW = ctx->gW.as<cx<T>>();
     a.gvw = ctx->gv.as<T>();
+    a.dgs = nullptr;
+    if (c.exclude_degenerate) {
+        MP3_CK(ctx->degen_grad.ensure(sizeof(cx<double>) * 4 * (size_t)nz * nz * nb));
+        a.dgs = ctx->degen_grad.as<cx<double>>();
+    }
     a.tabX = ctx->gtab.as<cx<T>>();
     a.tabY = a.tabX + ngroups * nb * nb;
     StageScope sc(ctx, ST_MOMENTS);
@@ -1317,8 +1323,6 @@ mp3pcf_status mp3pcf_moments_adjoint(mp3pcf_ctx* ctx, const double* d_grad_upsil
     if (!ctx || !d_grad_upsilon || !d_grad_norm) return fail(ctx, MP3PCF_EINVAL, "null argument");
     ctx->err.clear();
     if (n != ctx->n) return fail(ctx, MP3PCF_EINVAL, "n differs from the last accumulate call");
-    if (ctx->cfg.exclude_degenerate)
-        return fail(ctx, MP3PCF_EUNSUPPORTED, "the adjoint does not cover exclude_degenerate");
     if (n == 0) return MP3PCF_OK;
     if (!d_g1 || !d_g2 || !d_w) return fail(ctx, MP3PCF_EINVAL, "null catalog pointer");
     if (ctx->fp64) return moments_adjoint_t<double>(ctx, d_grad_upsilon, d_grad_norm, d_g1, d_g2, d_w, d_grad_g1,

@@ -179,6 +179,9 @@ struct AdjArgs {
     cx<T>* gW;
     T* gvw;                     // [n][4] per sorted galaxy: dL/dv (re, im; v = w gamma), direct
                                 // dL/dw, unused (16 bytes: one vector atomic per pair in FP32)
+    // exclude_degenerate: scratch for the gradients of the j = k sums, [n_z][n_z][nb][4] (NULL:
+    // the forward kept the j = k triplets, nothing to do)
+    cx<double>* dgs;
 };
 
 cudaError_t launch_moments_adjoint_f32(const AdjArgs<float>& a, int64_t n, const int* perm, const float* g1,

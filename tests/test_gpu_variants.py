@@ -1,5 +1,5 @@
 """exclude_degenerate (triplets with j = k left out) on the GPU against the oracle with the same
-flag, every output; the adjoint refuses the variant."""
+flag, every output; its adjoint against the oracle's FP64 autograd."""
 import numpy as np
 import pytest
 import torch
@@ -66,12 +66,33 @@ def test_exclude_degenerate_tomographic_fp64(gpu, orc):
     assert rel_err(g["m8"], r.m8) < 1e-10
 
 
-def test_adjoint_refuses_exclude_degenerate(gpu, noise2k):
-    from paper_2309_08601_gb300 import native
-    dev = gpu.catalog_to_device(noise2k)
+@pytest.mark.parametrize("precision,tol,n_z", [("fp64", 2e-6, 1), ("bf16x3", 1e-4, 1), ("fp64", 2e-6, 2)])
+def test_adjoint_excluding_degenerate_against_oracle_autograd(gpu, precision, tol, n_z):
+    """The differentiation form with exclude_degenerate: the whole chain's gradient (moments,
+    contraction, the j = k correction, edge correction, Gamma, Map^3) against the FP64 autograd of
+    the oracle, whose correction is pinned against the C oracle."""
+    import oracle
+    from oracle import torch_oracle as to
+    from tests._util import hand_catalog
+    rng = np.random.default_rng(21 + n_z)
+    n = 300
+    cat = hand_catalog(rng.uniform(0, 14, (n, 2)), rng.normal(0, .3, n) + 1j * rng.normal(0, .3, n),
+                       rng.uniform(0.5, 1.5, n), rng.integers(0, n_z, n) if n_z > 1 else None)
+    setup = dict(n_bins=6, theta_min=0.5, theta_max=8.0, n_max=5, n_phi=40, n_z=n_z)
+    th = [[2.0, 2.0, 2.0], [1.5, 2.5, 3.0]]
+    oracle.build_oracle()
+    mo = to.Map3Oracle(oracle.Setup(**setup, exclude_degenerate=1), cat, th, chunk_pairs=20_000)
+    c = np.random.default_rng(9).normal(size=(n_z ** 3, len(th), 8))
+    t64 = lambda a: torch.as_tensor(np.asarray(a, np.float64))
+    o1, o2, ow, _ = mo.grad(t64(cat.g1), t64(cat.g2), t64(cat.w), c)
+    dev = gpu.catalog_to_device(cat)
     g1 = dev[2].clone().requires_grad_(True)
-    with gpu.Estimator(**S0, precision="fp64", exclude_degenerate=1) as est:
-        m8 = gpu.map3(est, dev[0], dev[1], g1, dev[3], dev[4], TH0)
-        with pytest.raises(native.Mp3pcfError) as ei:
-            m8.sum().backward()
-        assert ei.value.status == native.EUNSUPPORTED
+    g2 = dev[3].clone().requires_grad_(True)
+    w = dev[4].clone().requires_grad_(True)
+    with gpu.Estimator(**setup, precision=precision, exclude_degenerate=1) as est:
+        m8 = gpu.map3(est, dev[0], dev[1], g1, g2, w, th, zbin=dev[5])
+        (torch.as_tensor(c, device="cuda") * m8).sum().backward()
+    errs = [rel_err(g1.grad.cpu().numpy(), o1.numpy()), rel_err(g2.grad.cpu().numpy(), o2.numpy()),
+            rel_err(w.grad.cpu().numpy(), ow.numpy())]
+    print(precision, n_z, "exclude_degenerate gradient errors vs FP64 autograd oracle", errs)
+    assert max(errs) < tol
