@@ -233,6 +233,58 @@ def measure_batch(api, n_real: int, precision: str, stream):
             "graph_launches": launches, "graph_instantiations": inst, "m8_finite": finite}
 
 
+def measure_combined(api, precision: str, stream):
+    """The combined estimator (Sec. 3.3) against the discrete one on the multiscale_310k workload
+    (the density and binning of the paper's accuracy test of it, a tenth of its area): moments and
+    contraction of each, timed with CUDA events after one untimed run; the levels start at 20
+    pixels of 0.25' and double the pixel every octave, as in that test."""
+    import torch
+    from paper_2309_08601_gb300 import synth
+    p = synth.WORKLOADS["multiscale_310k"]
+    cat = synth.workload_catalog("multiscale_310k")
+    dev = api.catalog_to_device(cat)
+    cset = dict(n_bins=p["n_bins"], theta_min=p["theta_min"], theta_max=p["theta_max"], n_max=p["n_max"])
+    with api.Estimator(**cset, precision=precision, stream=stream) as ec:
+        edges = ec.bin_edges()[0]
+        levels = synth.grid_levels(edges, int(round(p["grid_base_arcmin"] / synth.QUANTUM)), synth.QUANTUM)
+
+        def run(combined):
+            if combined:
+                ec.accumulate_moments_combined(*dev[:5], levels=levels)
+            else:
+                ec.accumulate_moments(*dev[:5])
+            return ec.contract()
+
+        out = {}
+        for combined in (False, True):
+            run(combined)
+            torch.cuda.synchronize()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            ups, norm = run(combined)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            out[combined] = (t0.elapsed_time(t1), ec.counts()[1], ups.cpu().numpy(), norm.cpu().numpy())
+    b0 = levels[0][0]
+    nb = p["n_bins"]
+    grid = np.zeros((nb, nb), bool)
+    grid[b0:, :] = grid[:, b0:] = True
+    ud, nd, uc, nc = out[False][2], out[False][3], out[True][2], out[True][3]
+
+    def nerr(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    return {"workload": "multiscale_310k: %d galaxies on %g' (noise-free lognormal), %d bins %g'-%g', n_max %d"
+                        % (cat.n, p["side"], nb, p["theta_min"], p["theta_max"], p["n_max"]),
+            "levels": [[int(b), float(q * synth.QUANTUM)] for b, q in levels],
+            "discrete_ms": out[False][0], "combined_ms": out[True][0], "speedup": out[False][0] / out[True][0],
+            "discrete_pairs": int(out[False][1]), "combined_pairs": int(out[True][1]),
+            "grid_blocks_rel_err_upsilon_n_le_10": nerr(uc[:, :, :11][..., grid], ud[:, :, :11][..., grid]),
+            "grid_blocks_rel_err_norm_n_le_20": nerr(nc[:, :21][..., grid], nd[:, :21][..., grid]),
+            "discrete_block_rel_err": float(np.abs(uc[..., ~grid] - ud[..., ~grid]).max() /
+                                            np.abs(ud[..., ~grid]).max())}
+
+
 def cpu_model() -> str:
     """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
     import platform
@@ -470,6 +522,10 @@ def run_gpu(args):
     if rank == 0 and args.batch_realisations > 0:
         line["batch"] = measure_batch(api, args.batch_realisations, args.precision, stream)
 
+    # ---- the combined estimator against the discrete one (rank 0)
+    if rank == 0 and args.combined:
+        line["combined"] = measure_combined(api, args.precision, stream)
+
     if rank == 0 and args.cpu_baseline:
         import oracle
         pr, sec, k, threads = oracle_sample(cat, setup, theta, target_s=args.cpu_s)
@@ -512,6 +568,8 @@ def main(argv=None):
                     help="skip the forward + backward timing of the differentiable Map^3")
     ap.add_argument("--batch-realisations", type=int, default=2,
                     help="tomographic realisations timed through mp3pcf_run_batch (0: skip)")
+    ap.add_argument("--no-combined", dest="combined", action="store_false",
+                    help="skip the combined-versus-discrete estimator timing")
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     ap.add_argument("--k1-traffic", type=float, default=None,
                     help="DRAM bytes per moments launch (default: the committed ncu figure, at "

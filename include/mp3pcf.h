@@ -187,6 +187,29 @@ mp3pcf_status mp3pcf_grid_catalog(mp3pcf_ctx* ctx, int64_t n, const int32_t* d_x
                                   int32_t* d_pxq, int32_t* d_pyq, float* d_pg1, float* d_pg2, float* d_pw,
                                   uint8_t* d_pzbin, int64_t* h_count);
 
+/* ---- Combined estimator (Sec. 3.3, Eq. CombinedEstimatorRegridding): the moments of the small
+ * radial bins from the galaxies and those of the large bins from pixel catalogs (the grid-based
+ * approximation above) of one or several resolutions. Level l (0 <= l < n_levels) covers bins
+ * [h_b_start[l], h_b_start[l + 1]) (the last level up to n_bins) with pixels of h_pixel_q[l]
+ * quanta on a grid whose origin is the lower corner of the catalog's extent (its bounding box,
+ * or the fixed extent of mp3pcf_set_extent); bins [0, h_b_start[0]) are the discrete moments of
+ * mp3pcf_accumulate_moments. For a centre galaxy i in pixel p_i of level l, its moments in the
+ * level's bins are the pixel catalog's moments about the centre of p_i (G_n^Delta(p_i), as they
+ * are: no division by the number of galaxies in the pixel); a galaxy whose pixel has no weight
+ * gets zeros there. mp3pcf_contract_multipoles then gives the paper's combined estimate: both
+ * bins discrete, Eq. CombinedEstimatorRegridding for one discrete and one grid bin, and
+ * Eq. UpsilonmuGrid (the pixels' own contraction) for two grid bins of one level. Arguments as in
+ * mp3pcf_accumulate_moments, plus n_levels >= 1, h_b_start (host, strictly increasing within
+ * [0, n_bins)) and h_pixel_q (host, pixel sides >= 1). The pair count of mp3pcf_counts adds the
+ * pixel pairs. Synchronises the stream once per level. EINVAL for bad levels or a grid of more
+ * than 2^31 - 1 pixels, EUNSUPPORTED with cfg.exclude_degenerate; after this call
+ * mp3pcf_moments_adjoint returns EUNSUPPORTED. */
+mp3pcf_status mp3pcf_accumulate_moments_combined(mp3pcf_ctx* ctx, int64_t n, const int32_t* d_xq,
+                                                 const int32_t* d_yq, const float* d_g1, const float* d_g2,
+                                                 const float* d_w, const uint8_t* d_zbin,
+                                                 const uint8_t* d_centre_mask, int32_t n_levels,
+                                                 const int32_t* h_b_start, const int64_t* h_pixel_q);
+
 /* ---- Direct estimator of the third-order aperture mass (Sec. 5.3, Eq. MapDirectEstimator), an
  * estimate of <M_ap^3> independent of the 3PCF route, for unmasked catalogs. For every aperture
  * centre t (d_centres [n_centres][2] double, arcmin, in the frame of the fixed-point positions:

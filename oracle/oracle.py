@@ -1,6 +1,8 @@
 """ctypes marshalling for the FP64 C oracle (``mp3pcf_oracle.c``). Test infrastructure only.
 
-Every function here converts numpy arrays to pointers and back; all arithmetic is in the C file.
+Most functions here convert numpy arrays to pointers and back, the arithmetic being in the C file;
+grid_catalog (per-pixel sums) and combined_moments (a copy of the pixel moments into the grid
+bins) are plain numpy steps around the C routines.
 """
 from __future__ import annotations
 
@@ -152,6 +154,44 @@ def grid_catalog(cat, origin, pixel_q: int, npx: int, npy: int, n_z: int = 1):
     return Catalog(pix_x.astype(np.int32), pix_y.astype(np.int32), (A[k] / W[k]).astype(np.float32),
                    (B[k] / W[k]).astype(np.float32), W[k].astype(np.float32),
                    None if n_z == 1 else (k // (npx * npy)).astype(np.uint8), 0.0, cat.quantum)
+
+
+def combined_moments(s: Setup, cat, levels, centres: Optional[np.ndarray] = None):
+    """The moments of the combined estimator (Sec. 3.3): level l = (b_start, pixel_q) of levels
+    covers the radial bins [b_start_l, b_start_{l+1}) (the last up to n_bins) with the pixel
+    catalog of side pixel_q quanta on the grid whose origin is the catalog's lower corner
+    (min xq, min yq); there a centre galaxy takes the moments of the pixel it lies in, evaluated
+    about the pixel centre (G_n^Delta at its pixel, with no division by the galaxies per pixel:
+    the reading under which Eq. CombinedEstimatorRegridding's two lines agree). The bins below the
+    first level keep the galaxies' discrete moments (Eq. Gn_disc). A galaxy whose pixel has no
+    weight gets zeros. Plain steps: all moments of the galaxies and of every pixel catalog, then a
+    copy of the levels' bins."""
+    if centres is None:
+        centres = np.arange(cat.n, dtype=np.int64)
+    centres = np.asarray(centres, dtype=np.int64)
+    G, W = moments(s, cat, centres)
+    xq = np.asarray(cat.xq, np.int64)
+    yq = np.asarray(cat.yq, np.int64)
+    z = np.zeros(cat.n, np.int64) if cat.zbin is None else np.asarray(cat.zbin, np.int64)
+    x0, y0 = int(xq.min()), int(yq.min())
+    for l, (b0, q) in enumerate(levels):
+        b1 = int(levels[l + 1][0]) if l + 1 < len(levels) else s.n_bins
+        q = int(q)
+        npx = (int(xq.max()) - x0) // q + 1
+        npy = (int(yq.max()) - y0) // q + 1
+        pix = grid_catalog(cat, (x0, y0), q, npx, npy, s.n_z)
+        Gp, Wp = moments(s, pix)
+        # the catalog index of each centre's pixel among the non-empty pixels ((z, iy, ix) order)
+        pid = ((z * npy + np.clip((yq - y0) // q, 0, npy - 1)) * npx + np.clip((xq - x0) // q, 0, npx - 1))[centres]
+        pz = np.zeros(pix.n, np.int64) if pix.zbin is None else np.asarray(pix.zbin, np.int64)
+        kid = (pz * npy + (np.asarray(pix.yq, np.int64) - y0) // q) * npx + (np.asarray(pix.xq, np.int64) - x0) // q
+        j = np.searchsorted(kid, pid)
+        ok = (j < pix.n) & (kid[np.minimum(j, max(pix.n - 1, 0))] == pid) if pix.n else np.zeros(len(pid), bool)
+        G[:, :, b0:b1, :] = 0
+        W[:, :, b0:b1, :] = 0
+        G[ok, :, b0:b1, :] = Gp[j[ok], :, b0:b1, :]
+        W[ok, :, b0:b1, :] = Wp[j[ok], :, b0:b1, :]
+    return G, W
 
 
 def num_threads() -> int:
@@ -345,5 +385,5 @@ def pipeline(s: Setup, cat, theta_ap, centres: Optional[np.ndarray] = None) -> R
 
 __all__ = ["Setup", "build_oracle", "edges", "moments", "count_pairs", "contract",
            "edge_correct", "degenerate_correction", "to_gamma", "to_map3", "filter_F", "cen_factor", "combine8", "brute",
-           "pipeline", "num_threads", "set_num_threads", "map3_direct", "grid_catalog", "Result",
+           "pipeline", "num_threads", "set_num_threads", "map3_direct", "grid_catalog", "combined_moments", "Result",
            "Brute"]

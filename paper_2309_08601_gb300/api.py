@@ -129,6 +129,29 @@ class Estimator:
                                                     _ptr(g2), _ptr(w), _ptr(zbin), _ptr(centre_mask))
         native.check(st, "mp3pcf_accumulate_moments", self._ctx)
 
+    def accumulate_moments_combined(self, xq, yq, g1, g2, w, zbin=None, centre_mask=None, levels=()):
+        """The combined estimator's moments (Sec. 3.3) through mp3pcf_accumulate_moments_combined:
+        levels is a sequence of (b_start, pixel_q); bins below the first b_start are the galaxies'
+        discrete moments, bins from b_start[l] on (up to the next level's) the moments of the
+        pixel catalog of side pixel_q quanta at each centre galaxy's pixel. contract() then gives
+        the combined multipoles."""
+        self._generation = getattr(self, "_generation", 0) + 1
+        torch = _torch()
+        n = int(xq.numel())
+        _need(xq, torch.int32, "xq", n)
+        _need(yq, torch.int32, "yq", n)
+        _need(g1, torch.float32, "g1", n)
+        _need(g2, torch.float32, "g2", n)
+        _need(w, torch.float32, "w", n)
+        _need(zbin, torch.uint8, "zbin", n)
+        _need(centre_mask, torch.uint8, "centre_mask", n)
+        L = len(levels)
+        bs = (C.c_int32 * max(L, 1))(*[int(b) for b, _ in levels])
+        pq = (C.c_int64 * max(L, 1))(*[int(q) for _, q in levels])
+        st = native.lib().mp3pcf_accumulate_moments_combined(self._ctx, n, _ptr(xq), _ptr(yq), _ptr(g1), _ptr(g2),
+                                                             _ptr(w), _ptr(zbin), _ptr(centre_mask), L, bs, pq)
+        native.check(st, "mp3pcf_accumulate_moments_combined", self._ctx)
+
     def counts(self):
         nc = C.c_int64()
         npairs = C.c_int64()

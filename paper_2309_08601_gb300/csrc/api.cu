@@ -378,6 +378,11 @@ struct mp3pcf_ctx {
     DevBuf zrange;                      // [nz + 1] centre range of each z-bin
     DevBuf gridsum;                     // per-pixel FP64 sums of the grid-based approximation
     DevBuf gridflag;                    // its non-empty flags and their exclusive scan
+    // combined estimator: the moments of the last accumulate call mix discrete and grid bins
+    bool combined = false;
+    long long bbox[4] = {0, 0, 0, 0};   // extent (x0, y0, x1, y1) of the last accumulate call
+    mp3pcf_ctx* sub = nullptr;          // context of the pixel catalogs (created on first use)
+    DevBuf pix, pixinv;                 // a pixel catalog (SoA) and its catalog index -> moment row
     // tracing: per-stage event pairs and kernel-launch counts
     bool timing = false;
     int64_t launches[6] = {0, 0, 0, 0, 0, 0};
@@ -557,8 +562,9 @@ mp3pcf_status mp3pcf_destroy(mp3pcf_ctx* ctx)
                       &ctx->G, &ctx->W, &ctx->pairs, &ctx->partial, &ctx->singular,
                       &ctx->m3partial, &ctx->ccoef, &ctx->gG, &ctx->gW, &ctx->gv, &ctx->gtab,
                       &ctx->adjscratch, &ctx->degen, &ctx->degen_grad, &ctx->zrange, &ctx->gridsum, &ctx->gridflag, &ctx->bups, &ctx->bnorm,
-                      &ctx->bgam, &ctx->bgcen, &ctx->berr};
+                      &ctx->bgam, &ctx->bgcen, &ctx->berr, &ctx->pix, &ctx->pixinv};
     for (DevBuf* b : bufs) b->release();
+    if (ctx->sub) mp3pcf_destroy(ctx->sub);
     if (ctx->batch_st) cudaStreamDestroy(ctx->batch_st);
     for (cudaEvent_t ev : ctx->batch_ev)
         if (ev) cudaEventDestroy(ev);
@@ -608,13 +614,14 @@ static unsigned grid1d(int64_t n, int n_sm)
 template <typename T>
 static mp3pcf_status accumulate_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq, const int32_t* yq,
                                   const float* g1, const float* g2, const float* w,
-                                  const uint8_t* zb, const uint8_t* mask)
+                                  const uint8_t* zb, const uint8_t* mask, int b_lo, int b_hi)
 {
     const mp3pcf_config& c = ctx->cfg;
     const int nz = c.n_z, nb = c.n_bins;
     cudaStream_t st = ctx->st;
     ctx->n = n;
     ctx->n_centres = 0;
+    ctx->combined = false;
     MP3_CK(cudaMemsetAsync(ctx->pairs.p, 0, 16, st));
     if (n == 0) return MP3PCF_OK;
     if (ctx->inject_alloc_failure) return fail(ctx, MP3PCF_ENOMEM, "injected allocation failure");
@@ -645,14 +652,16 @@ static mp3pcf_status accumulate_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq,
         stage_end(ctx, ST_SORT, t_sort);
         return fail(ctx, MP3PCF_EINVAL, "zbin value >= n_z");
     }
+    for (int i = 0; i < 4; ++i) ctx->bbox[i] = bb[i];
     const long long ex = (long long)bb[2] - bb[0], ey = (long long)bb[3] - bb[1];
     if (ex >= (1LL << 24) || ey >= (1LL << 24)) {
         stage_end(ctx, ST_SORT, t_sort);
         return fail(ctx, MP3PCF_EINVAL, "patch extent must be below 2^24 position quanta");
     }
 
-    // ---- cell grid: ~4 galaxies per cell and bin, and at most kMaxRows rows per annulus
-    const double R = sqrt((double)ctx->e2q[nb]);
+    // ---- cell grid: ~4 galaxies per cell and bin, and at most kMaxRows rows per annulus of the
+    // computed bins
+    const double R = sqrt((double)ctx->e2q[b_hi]);
     const double area = (double)(ex + 1) * (double)(ey + 1);
     const double occ = c.cell_occupancy > 0 ? (double)c.cell_occupancy : 4.0;
     double side = sqrt(area * occ / std::max(1.0, (double)n / nz));
@@ -731,12 +740,14 @@ static mp3pcf_status accumulate_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq,
     a.cell_start = ctx->count.as<int>();
     a.g = g;
     a.nz = nz;
-    a.nb = nb;
+    a.nb = b_hi - b_lo;
+    a.nbp = nb_pad(nb);
     a.n_max = c.n_max;
-    a.e2q = ctx->d_e2q.as<long long>();
-    a.G = ctx->G.as<cx<T>>();
-    a.W = ctx->W.as<cx<T>>();
+    a.e2q = ctx->d_e2q.as<long long>() + b_lo;
+    a.G = ctx->G.as<cx<T>>() + b_lo;
+    a.W = ctx->W.as<cx<T>>() + b_lo;
     a.pairs = ctx->pairs.as<unsigned long long>();
+    if (b_lo >= b_hi) return MP3PCF_OK;
     cudaError_t e;
     {
         StageScope sc(ctx, ST_MOMENTS);
@@ -764,8 +775,118 @@ mp3pcf_status mp3pcf_accumulate_moments(mp3pcf_ctx* ctx, int64_t n, const int32_
         return fail(ctx, MP3PCF_EINVAL, "null catalog pointer");
     if (ctx->cfg.n_z > 1 && n > 0 && !d_zbin)
         return fail(ctx, MP3PCF_EINVAL, "n_z > 1 needs zbin");
-    if (ctx->fp64) return accumulate_t<double>(ctx, n, d_xq, d_yq, d_g1, d_g2, d_w, d_zbin, d_centre_mask);
-    return accumulate_t<float>(ctx, n, d_xq, d_yq, d_g1, d_g2, d_w, d_zbin, d_centre_mask);
+    const int nb = ctx->cfg.n_bins;
+    if (ctx->fp64) return accumulate_t<double>(ctx, n, d_xq, d_yq, d_g1, d_g2, d_w, d_zbin, d_centre_mask, 0, nb);
+    return accumulate_t<float>(ctx, n, d_xq, d_yq, d_g1, d_g2, d_w, d_zbin, d_centre_mask, 0, nb);
+}
+
+}  // extern "C"
+
+// combined estimator (Sec. 3.3): bins [0, b_start[0]) from the galaxies, bins [b_start[l],
+// b_start[l + 1]) (the last level to n_bins) from the pixel catalog of side pixel_q[l] at the
+// pixel of each centre galaxy; the pixel catalogs' moments run in a second context
+template <typename T>
+static mp3pcf_status combined_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq, const int32_t* yq, const float* g1,
+                                const float* g2, const float* w, const uint8_t* zb, const uint8_t* mask, int L,
+                                const int32_t* b_start, const int64_t* pixel_q)
+{
+    const mp3pcf_config& c = ctx->cfg;
+    const int nz = c.n_z, nb = c.n_bins;
+    if (mp3pcf_status s = accumulate_t<T>(ctx, n, xq, yq, g1, g2, w, zb, mask, 0, b_start[0])) return s;
+    const int64_t nc = ctx->n_centres;
+    if (nc == 0) {
+        ctx->combined = true;
+        return MP3PCF_OK;
+    }
+    if (!ctx->sub) {
+        if (mp3pcf_status s = mp3pcf_create(&ctx->cfg, ctx->st, &ctx->sub))
+            return fail(ctx, s, "could not create the pixel catalogs' context");
+    }
+    mp3pcf_ctx* sub = ctx->sub;
+    const long long x0 = ctx->bbox[0], y0 = ctx->bbox[1];
+    for (int l = 0; l < L; ++l) {
+        const long long pq = pixel_q[l];
+        const int b0 = b_start[l], b1 = l + 1 < L ? b_start[l + 1] : nb;
+        const long long npx = (ctx->bbox[2] - x0) / pq + 1, npy = (ctx->bbox[3] - y0) / pq + 1;
+        const long long npix = (long long)nz * npx * npy;
+        if (npix > 0x7fffffffLL) return fail(ctx, MP3PCF_EINVAL, "a grid level has more than 2^31 - 1 pixels");
+        if (x0 + npx * pq > INT_MAX || y0 + npy * pq > INT_MAX)
+            return fail(ctx, MP3PCF_EINVAL, "a grid level lies outside the fixed-point range");
+        // pixel catalog (SoA xq, yq, g1, g2, w, zbin, centre mask) and the galaxies' pixels
+        MP3_CK(ctx->gridsum.ensure(sizeof(double) * 3 * (size_t)npix));
+        MP3_CK(ctx->gridflag.ensure(sizeof(int) * 2 * ((size_t)npix + 1)));
+        MP3_CK(ctx->pix.ensure(22 * (size_t)npix));
+        MP3_CK(ctx->pixinv.ensure(sizeof(int) * (size_t)npix));
+        int* flags = ctx->gridflag.as<int>();
+        int* rank = flags + npix + 1;
+        char* pb = ctx->pix.as<char>();
+        int32_t* pxq = (int32_t*)pb;
+        int32_t* pyq = (int32_t*)(pb + 4 * npix);
+        float* pg1 = (float*)(pb + 8 * npix);
+        float* pg2 = (float*)(pb + 12 * npix);
+        float* pw = (float*)(pb + 16 * npix);
+        uint8_t* pzb = (uint8_t*)(pb + 20 * npix);
+        uint8_t* pmask = (uint8_t*)(pb + 21 * npix);
+        const uint8_t* czs = nz > 1 ? ctx->zs.as<uint8_t>() : nullptr;
+        ctx->launches[ST_MOMENTS] += 7;
+        MP3_CK(launch_grid_sums(n, xq, yq, g1, g2, w, zb, nz, x0, y0, pq, (int)npx, (int)npy,
+                                ctx->gridsum.as<double>(), flags, ctx->n_sm, ctx->st));
+        if (mp3pcf_status s = scan_exclusive(ctx, flags, rank, npix)) return s;
+        MP3_CK(launch_grid_emit(nz, (int)npx, (int)npy, x0, y0, pq, ctx->gridsum.as<double>(), rank, pxq, pyq, pg1,
+                                pg2, pw, nz > 1 ? pzb : nullptr, ctx->n_sm, ctx->st));
+        MP3_CK(launch_grid_combine_map(nc, ctx->centre_idx.as<int>(), ctx->pos.as<int2>(), czs, x0, y0, pq, (int)npx,
+                                       (int)npy, flags, rank, npix, pmask, ctx->n_sm, ctx->st));
+        int cnt = 0;
+        MP3_CK(cudaMemcpyAsync(&cnt, rank + npix, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+        MP3_CK(cudaStreamSynchronize(ctx->st));
+        // the pixel catalog's moments of this level's bins
+        int64_t before[6];
+        for (int i = 0; i < 6; ++i) before[i] = sub->launches[i];
+        sub->inject_wait_timeout = ctx->inject_wait_timeout;
+        if (mp3pcf_status s = accumulate_t<T>(sub, cnt, pxq, pyq, pg1, pg2, pw, nz > 1 ? pzb : nullptr, pmask, b0, b1))
+            return fail(ctx, s, ("pixel catalog: " + sub->err).c_str());
+        for (int i = 0; i < 6; ++i) ctx->launches[i] += sub->launches[i] - before[i];
+        ctx->launches[ST_MOMENTS] += 3;
+        MP3_CK(launch_grid_gather<T>(nc, nz, nb, b0, b1, c.n_max, ctx->centre_idx.as<int>(), ctx->pos.as<int2>(), czs,
+                                     x0, y0, pq, (int)npx, (int)npy, flags, rank, sub->n_centres,
+                                     sub->centre_idx.as<int>(), sub->perm.as<int>(), ctx->pixinv.as<int>(),
+                                     sub->G.as<cx<T>>(), sub->W.as<cx<T>>(), ctx->G.as<cx<T>>(), ctx->W.as<cx<T>>(),
+                                     sub->pairs.as<unsigned long long>(), ctx->pairs.as<unsigned long long>(),
+                                     ctx->n_sm, ctx->st));
+    }
+    ctx->combined = true;
+    return MP3PCF_OK;
+}
+
+extern "C" {
+
+mp3pcf_status mp3pcf_accumulate_moments_combined(mp3pcf_ctx* ctx, int64_t n, const int32_t* d_xq,
+                                                 const int32_t* d_yq, const float* d_g1, const float* d_g2,
+                                                 const float* d_w, const uint8_t* d_zbin,
+                                                 const uint8_t* d_centre_mask, int32_t n_levels,
+                                                 const int32_t* h_b_start, const int64_t* h_pixel_q)
+{
+    if (!ctx) return MP3PCF_EINVAL;
+    ctx->err.clear();
+    const int nb = ctx->cfg.n_bins;
+    if (n < 0 || n > INT_MAX / 2) return fail(ctx, MP3PCF_EINVAL, "n out of range");
+    if (n > 0 && (!d_xq || !d_yq || !d_g1 || !d_g2 || !d_w))
+        return fail(ctx, MP3PCF_EINVAL, "null catalog pointer");
+    if (ctx->cfg.n_z > 1 && n > 0 && !d_zbin)
+        return fail(ctx, MP3PCF_EINVAL, "n_z > 1 needs zbin");
+    if (n_levels < 1 || !h_b_start || !h_pixel_q) return fail(ctx, MP3PCF_EINVAL, "no grid level");
+    for (int l = 0; l < n_levels; ++l) {
+        if (h_pixel_q[l] < 1 || h_pixel_q[l] > INT_MAX) return fail(ctx, MP3PCF_EINVAL, "pixel_q out of range");
+        if (h_b_start[l] < 0 || h_b_start[l] >= nb || (l > 0 && h_b_start[l] <= h_b_start[l - 1]))
+            return fail(ctx, MP3PCF_EINVAL, "b_start must increase strictly within [0, n_bins)");
+    }
+    if (ctx->cfg.exclude_degenerate)
+        return fail(ctx, MP3PCF_EUNSUPPORTED, "the combined estimator does not take exclude_degenerate");
+    if (ctx->fp64)
+        return combined_t<double>(ctx, n, d_xq, d_yq, d_g1, d_g2, d_w, d_zbin, d_centre_mask, n_levels, h_b_start,
+                                  h_pixel_q);
+    return combined_t<float>(ctx, n, d_xq, d_yq, d_g1, d_g2, d_w, d_zbin, d_centre_mask, n_levels, h_b_start,
+                             h_pixel_q);
 }
 
 mp3pcf_status mp3pcf_counts(mp3pcf_ctx* ctx, int64_t* h_n_centres, int64_t* h_n_pairs)
@@ -1323,6 +1444,7 @@ mp3pcf_status mp3pcf_moments_adjoint(mp3pcf_ctx* ctx, const double* d_grad_upsil
     if (!ctx || !d_grad_upsilon || !d_grad_norm) return fail(ctx, MP3PCF_EINVAL, "null argument");
     ctx->err.clear();
     if (n != ctx->n) return fail(ctx, MP3PCF_EINVAL, "n differs from the last accumulate call");
+    if (ctx->combined) return fail(ctx, MP3PCF_EUNSUPPORTED, "no adjoint of the combined estimator's grid bins");
     if (n == 0) return MP3PCF_OK;
     if (!d_g1 || !d_g2 || !d_w) return fail(ctx, MP3PCF_EINVAL, "null catalog pointer");
     if (ctx->fp64) return moments_adjoint_t<double>(ctx, d_grad_upsilon, d_grad_norm, d_g1, d_g2, d_w, d_grad_g1,

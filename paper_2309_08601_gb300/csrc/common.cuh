@@ -87,10 +87,11 @@ struct MomentArgs {
     const Pay<T>* pay;          // sorted (w gamma_1, w gamma_2, w)
     const int32_t* cell_start;  // [n_z * ncells + 1], key = zbin * ncells + cy * ncx + cx
     GridDesc g;
-    int32_t nz, nb, n_max;
-    const long long* e2q;       // [nb + 1] exact squared edges in fixed-point units^2
-    cx<T>* G;                   // [2 n_max + 3][n_centres][nz][nb_pad(nb)]
-    cx<T>* W;                   // [2 n_max + 1][n_centres][nz][nb_pad(nb)]
+    int32_t nz, nb, n_max;      // nb: the radial bins computed, a range [b_lo, b_lo + nb) of the layout's
+    int32_t nbp;                // bins per row of the layout (nb_pad of all its bins)
+    const long long* e2q;       // [nb + 1] exact squared edges in fixed-point units^2, from bin b_lo
+    cx<T>* G;                   // [2 n_max + 3][n_centres][nz][nbp], offset to bin b_lo
+    cx<T>* W;                   // [2 n_max + 1][n_centres][nz][nbp], offset to bin b_lo
     unsigned long long* pairs;  // [0] pair counter, [1] error flags (1: a bounded wait gave up)
 };
 
@@ -147,6 +148,19 @@ cudaError_t launch_grid_sums(int64_t n, const int32_t* xq, const int32_t* yq, co
 cudaError_t launch_grid_emit(int nz, int npx, int npy, long long x0, long long y0, long long pq, const double* scratch,
                              const int* rank, int32_t* oxq, int32_t* oyq, float* og1, float* og2, float* ow,
                              uint8_t* ozb, int n_sm, cudaStream_t st);
+// combined estimator (Sec. 3.3): the pixels that hold a centre galaxy (pmask over the pixel catalog)
+cudaError_t launch_grid_combine_map(int64_t nc, const int* centre_idx, const int2* pos, const uint8_t* zs,
+                                    long long x0, long long y0, long long pq, int npx, int npy, const int* flags,
+                                    const int* rank, int64_t n_pix, uint8_t* pmask, int n_sm, cudaStream_t st);
+// rows [b0, b1) of every centre's G, W from the moments of its pixel; also merges the pixel
+// catalog's pair counter and error flags into pairs
+template <typename T>
+cudaError_t launch_grid_gather(int64_t nc, int nz, int nb, int b0, int b1, int n_max, const int* centre_idx,
+                               const int2* pos, const uint8_t* zs, long long x0, long long y0, long long pq, int npx,
+                               int npy, const int* flags, const int* rank, int64_t nsub, const int* sub_centre_idx,
+                               const int* sub_perm, int* inv, const cx<T>* Gs, const cx<T>* Ws, cx<T>* G, cx<T>* W,
+                               const unsigned long long* sub_pairs, unsigned long long* pairs, int n_sm,
+                               cudaStream_t st);
 // direct estimator of <M_ap^3> (Sec. 5.3): out[centre][radii triple][2] = (numerator, denominator)
 cudaError_t launch_map3_direct(int64_t n, const int32_t* xq, const int32_t* yq, const float* g1, const float* g2,
                                const float* w, double quantum, int64_t n_cen, const double* centres, int n_ap,

@@ -64,6 +64,86 @@ __global__ void k_grid_emit(int64_t npix, int npx, int npy, long long x0, long l
     }
 }
 
+// ---- combined estimator (Sec. 3.3): the moments of the bins that use the grid are, for every
+// centre galaxy, those of the pixel it lies in (the value G_n^Delta at its pixel, taken as it is:
+// Eq. CombinedEstimatorRegridding holds without a division by the galaxies per pixel)
+
+// the pixel of a galaxy at fixed-point (x, y) in z-bin z, by the same rule as k_grid_scatter
+__device__ __forceinline__ int64_t grid_pixel(int x, int y, int z, long long x0, long long y0, long long pq,
+                                              int npx, int npy)
+{
+    const long long dx = (long long)x - x0, dy = (long long)y - y0;
+    const int ix = (int)min(max(dx < 0 ? -1LL : dx / pq, 0LL), (long long)npx - 1);
+    const int iy = (int)min(max(dy < 0 ? -1LL : dy / pq, 0LL), (long long)npy - 1);
+    return ((int64_t)z * npy + iy) * npx + ix;
+}
+
+// pmask[q] = 1 for the pixels (catalog index q) that hold a centre galaxy; pmask zeroed before
+__global__ void k_grid_centre_mask(int64_t nc, const int* __restrict__ centre_idx, const int2* __restrict__ pos,
+                                   const uint8_t* __restrict__ zs, long long x0, long long y0, long long pq,
+                                   int npx, int npy, const int* __restrict__ flags, const int* __restrict__ rank,
+                                   uint8_t* __restrict__ pmask)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        const int j = centre_idx[c];
+        const int2 p = pos[j];
+        const int64_t pid = grid_pixel(p.x, p.y, zs ? (int)zs[j] : 0, x0, y0, pq, npx, npy);
+        if (flags[pid]) pmask[rank[pid]] = 1;
+    }
+}
+
+// inv[q] = the moment row of pixel q in the pixel catalog's context (its rows are its centres in
+// sorted order; perm maps a sorted position to the catalog index)
+__global__ void k_grid_invert(int64_t nrows, const int* __restrict__ centre_idx, const int* __restrict__ perm,
+                              int* __restrict__ inv)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * blockDim.x)
+        inv[perm[centre_idx[r]]] = (int)r;
+}
+
+// rows [b0, b1) of G (order slots [0, lg)) and W (slots [0, lw)) of every centre from the pixel
+// moments Gs, Ws ([slot][nsub][nz][nb_pad]); a galaxy whose pixel has no weight (W <= 0, not in
+// the pixel catalog) gets zeros
+template <typename T>
+__global__ void k_grid_gather(int64_t nc, int nz, int nb, int b0, int b1, int lg, int lw,
+                              const int* __restrict__ centre_idx, const int2* __restrict__ pos,
+                              const uint8_t* __restrict__ zs, long long x0, long long y0, long long pq, int npx,
+                              int npy, const int* __restrict__ flags, const int* __restrict__ rank,
+                              const int* __restrict__ inv, int64_t nsub, const cx<T>* __restrict__ Gs,
+                              const cx<T>* __restrict__ Ws, cx<T>* __restrict__ G, cx<T>* __restrict__ W)
+{
+    const int nbp = nb_pad(nb), nbr = b1 - b0;
+    const int64_t total = (int64_t)lg * nc * nz * nbr;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int b = b0 + (int)(t % nbr);
+        int64_t r = t / nbr;
+        const int z = (int)(r % nz);
+        r /= nz;
+        const int64_t c = r % nc;
+        const int q = (int)(r / nc);
+        const int j = centre_idx[c];
+        const int2 p = pos[j];
+        const int64_t pid = grid_pixel(p.x, p.y, zs ? (int)zs[j] : 0, x0, y0, pq, npx, npy);
+        const int64_t dst = (((int64_t)q * nc + c) * nz + z) * nbp + b;
+        cx<T> g{T(0), T(0)}, v{T(0), T(0)};
+        if (flags[pid]) {
+            const int64_t src = (((int64_t)q * nsub + inv[rank[pid]]) * nz + z) * nbp + b;
+            g = Gs[src];
+            if (q < lw) v = Ws[src];
+        }
+        G[dst] = g;
+        if (q < lw) W[dst] = v;
+    }
+}
+
+// the pixel catalog's pair count and error flags added to the galaxy catalog's
+__global__ void k_merge_counters(const unsigned long long* __restrict__ from, unsigned long long* __restrict__ to)
+{
+    to[0] += from[0];
+    to[1] |= from[1];
+}
+
 static unsigned grid_blocks(int64_t m, int n_sm)
 {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, (int64_t)n_sm * 16));
@@ -91,5 +171,46 @@ cudaError_t launch_grid_emit(int nz, int npx, int npy, long long x0, long long y
                                                           og2, ow, ozb);
     return cudaGetLastError();
 }
+
+cudaError_t launch_grid_combine_map(int64_t nc, const int* centre_idx, const int2* pos, const uint8_t* zs,
+                                    long long x0, long long y0, long long pq, int npx, int npy, const int* flags,
+                                    const int* rank, int64_t n_pix, uint8_t* pmask, int n_sm, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(pmask, 0, (size_t)n_pix, st);
+    if (e != cudaSuccess) return e;
+    k_grid_centre_mask<<<grid_blocks(nc, n_sm), 256, 0, st>>>(nc, centre_idx, pos, zs, x0, y0, pq, npx, npy, flags,
+                                                               rank, pmask);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_grid_gather(int64_t nc, int nz, int nb, int b0, int b1, int n_max, const int* centre_idx,
+                               const int2* pos, const uint8_t* zs, long long x0, long long y0, long long pq, int npx,
+                               int npy, const int* flags, const int* rank, int64_t nsub, const int* sub_centre_idx,
+                               const int* sub_perm, int* inv, const cx<T>* Gs, const cx<T>* Ws, cx<T>* G, cx<T>* W,
+                               const unsigned long long* sub_pairs, unsigned long long* pairs, int n_sm,
+                               cudaStream_t st)
+{
+    k_merge_counters<<<1, 1, 0, st>>>(sub_pairs, pairs);
+    if (nsub > 0)
+        k_grid_invert<<<grid_blocks(nsub, n_sm), 256, 0, st>>>(nsub, sub_centre_idx, sub_perm, inv);
+    const int lg = 2 * n_max + 3, lw = 2 * n_max + 1;
+    if (nc > 0 && b1 > b0)
+        k_grid_gather<T><<<grid_blocks((int64_t)lg * nc * nz * (b1 - b0), n_sm), 256, 0, st>>>(
+            nc, nz, nb, b0, b1, lg, lw, centre_idx, pos, zs, x0, y0, pq, npx, npy, flags, rank, inv, nsub, Gs, Ws, G,
+            W);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_grid_gather<float>(int64_t, int, int, int, int, int, const int*, const int2*,
+                                               const uint8_t*, long long, long long, long long, int, int, const int*,
+                                               const int*, int64_t, const int*, const int*, int*, const cx<float>*,
+                                               const cx<float>*, cx<float>*, cx<float>*,
+                                               const unsigned long long*, unsigned long long*, int, cudaStream_t);
+template cudaError_t launch_grid_gather<double>(int64_t, int, int, int, int, int, const int*, const int2*,
+                                                const uint8_t*, long long, long long, long long, int, int, const int*,
+                                                const int*, int64_t, const int*, const int*, int*,
+                                                const cx<double>*, const cx<double>*, cx<double>*, cx<double>*,
+                                                const unsigned long long*, unsigned long long*, int, cudaStream_t);
 
 }  // namespace mp3

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(MomPlan<T, NMAX>::NT, MomPlan<T, NMAX>::MINB) 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int nb = A.nb, nz = A.nz, n_max = A.n_max;
-    const size_t plane = (size_t)A.n_centres * nz * nb_pad(nb);  // stride between order slots
+    const size_t plane = (size_t)A.n_centres * nz * A.nbp;  // stride between order slots
     const float S = (float)A.g.side, iS = 1.0f / S;
     // the last order slot of this warp may fall outside the order range
     const bool lastW = warp + (NWM - 1) * P <= 2 * NMAX;
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(MomPlan<T, NMAX>::NT, MomPlan<T, NMAX>::MINB) 
 #pragma unroll
                 for (int i = 0; i < PER; ++i) st[lane * PER + i] = acc[i];
                 __syncwarp();
-                const size_t row = ((size_t)c * nz + z) * nb_pad(nb) + b;
+                const size_t row = ((size_t)c * nz + z) * A.nbp + b;
                 cx<T>* Gp = A.G + row;  // order slot q at Gp[q * plane]
                 cx<T>* Wp = A.W + row;
                 if (lane < NWM) {

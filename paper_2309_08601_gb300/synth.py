@@ -215,10 +215,34 @@ WORKLOADS = {
     "grad_lognormal_500k": dict(n=500_000, side=420.0, field="lognormal", weights="uniform",
                                 seed=4, n_bins=20, theta_min=0.5, theta_max=120.0, n_max=30,
                                 theta_ap=[4.0, 8.0, 16.0]),
+    # the density and binning of the combined estimator's accuracy test (3.1e6 galaxies on
+    # 100 deg^2, 33 logarithmic bins 0.25'-80', noise-free) on a tenth of the area
+    "multiscale_310k": dict(n=310_000, side=190.0, field="lognormal", weights="uniform", seed=5,
+                            sigma_e=0.0, n_bins=33, theta_min=0.25, theta_max=80.0, n_max=30,
+                            grid_base_arcmin=0.25),
 }
+
+
+def grid_levels(edges, base_q: int, quantum: float):
+    """The combined estimator's levels (b_start, pixel_q) for bin edges (arcmin), as in the
+    paper's accuracy test of it: pixels of side Delta (base_q quanta first) for the bins with
+    20 Delta <= lower edge < 40 Delta, then 2 Delta, and so on; the bins below 20 base_q stay
+    discrete."""
+    levels = []
+    d = int(base_q)
+    for b in range(len(edges) - 1):
+        lo = float(edges[b]) / quantum
+        if lo < 20 * base_q:
+            continue
+        while lo >= 40 * d:
+            d *= 2
+        if not levels or levels[-1][1] != d:
+            levels.append((b, d))
+    return levels
 
 
 def workload_catalog(name: str, ngrid: int = 4096, n: Optional[int] = None) -> Catalog:
     p = WORKLOADS[name]
     return make_catalog(n if n is not None else p["n"], p["side"], p["seed"], field=p["field"],
-                        weights=p["weights"], ngrid=ngrid, holes=p.get("holes", False))
+                        weights=p["weights"], ngrid=ngrid, holes=p.get("holes", False),
+                        sigma_e=p.get("sigma_e", 0.26))
