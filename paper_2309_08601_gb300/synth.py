@@ -223,18 +223,18 @@ WORKLOADS = {
 }
 
 
-def grid_levels(edges, base_q: int, quantum: float):
+def grid_levels(edges, base_q: int, quantum: float, ratio: float = 20.0):
     """The combined estimator's levels (b_start, pixel_q) for bin edges (arcmin), as in the
-    paper's accuracy test of it: pixels of side Delta (base_q quanta first) for the bins with
-    20 Delta <= lower edge < 40 Delta, then 2 Delta, and so on; the bins below 20 base_q stay
-    discrete."""
+    paper's accuracy test of it (ratio 20): pixels of side Delta (base_q quanta first) for the
+    bins with ratio Delta <= lower edge < 2 ratio Delta, then 2 Delta, and so on; the bins below
+    ratio base_q stay discrete."""
     levels = []
     d = int(base_q)
     for b in range(len(edges) - 1):
         lo = float(edges[b]) / quantum
-        if lo < 20 * base_q:
+        if lo < ratio * base_q:
             continue
-        while lo >= 40 * d:
+        while lo >= 2 * ratio * d:
             d *= 2
         if not levels or levels[-1][1] != d:
             levels.append((b, d))

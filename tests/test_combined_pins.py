@@ -87,3 +87,5 @@ def test_grid_levels_follow_the_octave_rule():
         for bb in range(b, last):
             assert 20 * d <= edges[bb] / q < 40 * d
     assert edges[lv[0][0] - 1] / q < 20 * (1 << 11)
+    # twice the pixels per bin: the same discrete range on pixels half the size
+    assert synth.grid_levels(edges, 1 << 10, q, ratio=40) == [(b, d // 2) for b, d in lv]
