@@ -382,8 +382,13 @@ class Estimator:
 
     # ------------------------------------------------------------------ whole path
     def measure(self, xq, yq, g1, g2, w, theta_ap, zbin=None, centre_mask=None,
-                report_singular=True) -> Measurement:
-        self.accumulate_moments(xq, yq, g1, g2, w, zbin, centre_mask)
+                report_singular=True, levels=None) -> Measurement:
+        """The whole path for one catalog; with levels ((b_start, pixel_q), ...) the moments are
+        the combined estimator's (accumulate_moments_combined)."""
+        if levels:
+            self.accumulate_moments_combined(xq, yq, g1, g2, w, zbin, centre_mask, levels=levels)
+        else:
+            self.accumulate_moments(xq, yq, g1, g2, w, zbin, centre_mask)
         ups, norm = self.contract()
         gam, ns = self.edge_correct(ups, norm, report_singular)
         gx = self.to_gamma(gam, 0)
