@@ -382,7 +382,7 @@ struct mp3pcf_ctx {
     bool combined = false;
     long long bbox[4] = {0, 0, 0, 0};   // extent (x0, y0, x1, y1) of the last accumulate call
     mp3pcf_ctx* sub = nullptr;          // context of the pixel catalogs (created on first use)
-    DevBuf pix, pixinv;                 // a pixel catalog (SoA) and its catalog index -> moment row
+    DevBuf pix, pixinv;                 // a pixel catalog (SoA); its catalog index -> moment row, then each centre's row
     // tracing: per-stage event pairs and kernel-launch counts
     bool timing = false;
     int64_t launches[6] = {0, 0, 0, 0, 0, 0};
@@ -816,7 +816,7 @@ static mp3pcf_status combined_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq, c
         MP3_CK(ctx->gridsum.ensure(sizeof(double) * 3 * (size_t)npix));
         MP3_CK(ctx->gridflag.ensure(sizeof(int) * 2 * ((size_t)npix + 1)));
         MP3_CK(ctx->pix.ensure(22 * (size_t)npix));
-        MP3_CK(ctx->pixinv.ensure(sizeof(int) * (size_t)npix));
+        MP3_CK(ctx->pixinv.ensure(sizeof(int) * ((size_t)npix + (size_t)nc)));
         int* flags = ctx->gridflag.as<int>();
         int* rank = flags + npix + 1;
         char* pb = ctx->pix.as<char>();
@@ -828,7 +828,7 @@ static mp3pcf_status combined_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq, c
         uint8_t* pzb = (uint8_t*)(pb + 20 * npix);
         uint8_t* pmask = (uint8_t*)(pb + 21 * npix);
         const uint8_t* czs = nz > 1 ? ctx->zs.as<uint8_t>() : nullptr;
-        ctx->launches[ST_MOMENTS] += 7;
+        ctx->launches[ST_MOMENTS] += 8;
         MP3_CK(launch_grid_sums(n, xq, yq, g1, g2, w, zb, nz, x0, y0, pq, (int)npx, (int)npy,
                                 ctx->gridsum.as<double>(), flags, ctx->n_sm, ctx->st));
         if (mp3pcf_status s = scan_exclusive(ctx, flags, rank, npix)) return s;
@@ -846,11 +846,11 @@ static mp3pcf_status combined_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq, c
         if (mp3pcf_status s = accumulate_t<T>(sub, cnt, pxq, pyq, pg1, pg2, pw, nz > 1 ? pzb : nullptr, pmask, b0, b1))
             return fail(ctx, s, ("pixel catalog: " + sub->err).c_str());
         for (int i = 0; i < 6; ++i) ctx->launches[i] += sub->launches[i] - before[i];
-        ctx->launches[ST_MOMENTS] += 3;
+        ctx->launches[ST_MOMENTS] += 4;
         MP3_CK(launch_grid_gather<T>(nc, nz, nb, b0, b1, c.n_max, ctx->centre_idx.as<int>(), ctx->pos.as<int2>(), czs,
                                      x0, y0, pq, (int)npx, (int)npy, flags, rank, sub->n_centres,
                                      sub->centre_idx.as<int>(), sub->perm.as<int>(), ctx->pixinv.as<int>(),
-                                     sub->G.as<cx<T>>(), sub->W.as<cx<T>>(), ctx->G.as<cx<T>>(), ctx->W.as<cx<T>>(),
+                                     ctx->pixinv.as<int>() + npix, sub->G.as<cx<T>>(), sub->W.as<cx<T>>(), ctx->G.as<cx<T>>(), ctx->W.as<cx<T>>(),
                                      sub->pairs.as<unsigned long long>(), ctx->pairs.as<unsigned long long>(),
                                      ctx->n_sm, ctx->st));
     }
@@ -882,6 +882,7 @@ mp3pcf_status mp3pcf_accumulate_moments_combined(mp3pcf_ctx* ctx, int64_t n, con
     }
     if (ctx->cfg.exclude_degenerate)
         return fail(ctx, MP3PCF_EUNSUPPORTED, "the combined estimator does not take exclude_degenerate");
+    NvtxRange nvtx("mp3pcf accumulate_moments_combined");
     if (ctx->fp64)
         return combined_t<double>(ctx, n, d_xq, d_yq, d_g1, d_g2, d_w, d_zbin, d_centre_mask, n_levels, h_b_start,
                                   h_pixel_q);

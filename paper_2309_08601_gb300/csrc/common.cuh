@@ -158,8 +158,8 @@ template <typename T>
 cudaError_t launch_grid_gather(int64_t nc, int nz, int nb, int b0, int b1, int n_max, const int* centre_idx,
                                const int2* pos, const uint8_t* zs, long long x0, long long y0, long long pq, int npx,
                                int npy, const int* flags, const int* rank, int64_t nsub, const int* sub_centre_idx,
-                               const int* sub_perm, int* inv, const cx<T>* Gs, const cx<T>* Ws, cx<T>* G, cx<T>* W,
-                               const unsigned long long* sub_pairs, unsigned long long* pairs, int n_sm,
+                               const int* sub_perm, int* inv, int* srow, const cx<T>* Gs, const cx<T>* Ws, cx<T>* G,
+                               cx<T>* W, const unsigned long long* sub_pairs, unsigned long long* pairs, int n_sm,
                                cudaStream_t st);
 // direct estimator of <M_ap^3> (Sec. 5.3): out[centre][radii triple][2] = (numerator, denominator)
 cudaError_t launch_map3_direct(int64_t n, const int32_t* xq, const int32_t* yq, const float* g1, const float* g2,

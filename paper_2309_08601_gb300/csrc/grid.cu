@@ -101,34 +101,43 @@ __global__ void k_grid_invert(int64_t nrows, const int* __restrict__ centre_idx,
         inv[perm[centre_idx[r]]] = (int)r;
 }
 
-// rows [b0, b1) of G (order slots [0, lg)) and W (slots [0, lw)) of every centre from the pixel
-// moments Gs, Ws ([slot][nsub][nz][nb_pad]); a galaxy whose pixel has no weight (W <= 0, not in
-// the pixel catalog) gets zeros
-template <typename T>
-__global__ void k_grid_gather(int64_t nc, int nz, int nb, int b0, int b1, int lg, int lw,
-                              const int* __restrict__ centre_idx, const int2* __restrict__ pos,
-                              const uint8_t* __restrict__ zs, long long x0, long long y0, long long pq, int npx,
-                              int npy, const int* __restrict__ flags, const int* __restrict__ rank,
-                              const int* __restrict__ inv, int64_t nsub, const cx<T>* __restrict__ Gs,
-                              const cx<T>* __restrict__ Ws, cx<T>* __restrict__ G, cx<T>* __restrict__ W)
+// srow[c] = the moment row, in the pixel catalog's context, of the pixel centre c lies in, or -1
+// when that pixel has no weight (W <= 0, not in the pixel catalog)
+__global__ void k_grid_rows(int64_t nc, const int* __restrict__ centre_idx, const int2* __restrict__ pos,
+                            const uint8_t* __restrict__ zs, long long x0, long long y0, long long pq, int npx,
+                            int npy, const int* __restrict__ flags, const int* __restrict__ rank,
+                            const int* __restrict__ inv, int* __restrict__ srow)
 {
-    const int nbp = nb_pad(nb), nbr = b1 - b0;
-    const int64_t total = (int64_t)lg * nc * nz * nbr;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int b = b0 + (int)(t % nbr);
-        int64_t r = t / nbr;
-        const int z = (int)(r % nz);
-        r /= nz;
-        const int64_t c = r % nc;
-        const int q = (int)(r / nc);
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
         const int j = centre_idx[c];
         const int2 p = pos[j];
         const int64_t pid = grid_pixel(p.x, p.y, zs ? (int)zs[j] : 0, x0, y0, pq, npx, npy);
-        const int64_t dst = (((int64_t)q * nc + c) * nz + z) * nbp + b;
+        srow[c] = flags[pid] ? inv[rank[pid]] : -1;
+    }
+}
+
+// rows [b0, b0 + nbr) of G (order slots [0, lg)) and W (slots [0, lw)) of every centre from the
+// pixel moments Gs, Ws ([slot][nsub][nz][nbp]), zeros where srow < 0. Order slot q = blockIdx.y;
+// the threads run over (centre, z, bin) with the bin fastest, so a warp writes whole runs of
+// bins; I is the index type (32-bit when nc nz nbr fits)
+template <typename T, typename I>
+__global__ void k_grid_copy(I ncz, int nz, int nbp, int b0, int nbr, int lw, const int* __restrict__ srow,
+                            int64_t nsub, const cx<T>* __restrict__ Gs, const cx<T>* __restrict__ Ws,
+                            cx<T>* __restrict__ G, cx<T>* __restrict__ W)
+{
+    const int q = blockIdx.y;
+    const I total = ncz * (I)nbr;
+    const int64_t nc = (int64_t)(ncz / (I)nz);
+    for (I t = blockIdx.x * (I)blockDim.x + threadIdx.x; t < total; t += (I)gridDim.x * blockDim.x) {
+        const I cz = t / (I)nbr;
+        const int b = b0 + (int)(t - cz * (I)nbr);
+        const I c = cz / (I)nz;
+        const int z = (int)(cz - c * (I)nz);
+        const int r = srow[c];
+        const int64_t dst = (((int64_t)q * nc + (int64_t)c) * nz + z) * nbp + b;
         cx<T> g{T(0), T(0)}, v{T(0), T(0)};
-        if (flags[pid]) {
-            const int64_t src = (((int64_t)q * nsub + inv[rank[pid]]) * nz + z) * nbp + b;
+        if (r >= 0) {
+            const int64_t src = (((int64_t)q * nsub + r) * nz + z) * nbp + b;
             g = Gs[src];
             if (q < lw) v = Ws[src];
         }
@@ -187,29 +196,37 @@ template <typename T>
 cudaError_t launch_grid_gather(int64_t nc, int nz, int nb, int b0, int b1, int n_max, const int* centre_idx,
                                const int2* pos, const uint8_t* zs, long long x0, long long y0, long long pq, int npx,
                                int npy, const int* flags, const int* rank, int64_t nsub, const int* sub_centre_idx,
-                               const int* sub_perm, int* inv, const cx<T>* Gs, const cx<T>* Ws, cx<T>* G, cx<T>* W,
-                               const unsigned long long* sub_pairs, unsigned long long* pairs, int n_sm,
+                               const int* sub_perm, int* inv, int* srow, const cx<T>* Gs, const cx<T>* Ws, cx<T>* G,
+                               cx<T>* W, const unsigned long long* sub_pairs, unsigned long long* pairs, int n_sm,
                                cudaStream_t st)
 {
     k_merge_counters<<<1, 1, 0, st>>>(sub_pairs, pairs);
     if (nsub > 0)
         k_grid_invert<<<grid_blocks(nsub, n_sm), 256, 0, st>>>(nsub, sub_centre_idx, sub_perm, inv);
     const int lg = 2 * n_max + 3, lw = 2 * n_max + 1;
-    if (nc > 0 && b1 > b0)
-        k_grid_gather<T><<<grid_blocks((int64_t)lg * nc * nz * (b1 - b0), n_sm), 256, 0, st>>>(
-            nc, nz, nb, b0, b1, lg, lw, centre_idx, pos, zs, x0, y0, pq, npx, npy, flags, rank, inv, nsub, Gs, Ws, G,
-            W);
+    if (nc > 0 && b1 > b0) {
+        k_grid_rows<<<grid_blocks(nc, n_sm), 256, 0, st>>>(nc, centre_idx, pos, zs, x0, y0, pq, npx, npy, flags,
+                                                           rank, inv, srow);
+        const int64_t ncz = nc * nz, m = ncz * (b1 - b0);
+        const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, 4LL * n_sm)), lg);
+        if (m < 0x7fffffffLL)
+            k_grid_copy<T, uint32_t><<<grid, 256, 0, st>>>((uint32_t)ncz, nz, nb_pad(nb), b0, b1 - b0, lw, srow,
+                                                           nsub, Gs, Ws, G, W);
+        else
+            k_grid_copy<T, int64_t><<<grid, 256, 0, st>>>(ncz, nz, nb_pad(nb), b0, b1 - b0, lw, srow, nsub, Gs, Ws,
+                                                          G, W);
+    }
     return cudaGetLastError();
 }
 
 template cudaError_t launch_grid_gather<float>(int64_t, int, int, int, int, int, const int*, const int2*,
                                                const uint8_t*, long long, long long, long long, int, int, const int*,
-                                               const int*, int64_t, const int*, const int*, int*, const cx<float>*,
-                                               const cx<float>*, cx<float>*, cx<float>*,
+                                               const int*, int64_t, const int*, const int*, int*, int*,
+                                               const cx<float>*, const cx<float>*, cx<float>*, cx<float>*,
                                                const unsigned long long*, unsigned long long*, int, cudaStream_t);
 template cudaError_t launch_grid_gather<double>(int64_t, int, int, int, int, int, const int*, const int2*,
                                                 const uint8_t*, long long, long long, long long, int, int, const int*,
-                                                const int*, int64_t, const int*, const int*, int*,
+                                                const int*, int64_t, const int*, const int*, int*, int*,
                                                 const cx<double>*, const cx<double>*, cx<double>*, cx<double>*,
                                                 const unsigned long long*, unsigned long long*, int, cudaStream_t);
 
