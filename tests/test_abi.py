@@ -81,3 +81,25 @@ def test_null_context_calls_fail_cleanly(lib):
     assert L.mp3pcf_accumulate_moments(None, 0, None, None, None, None, None, None, None) == lib.EINVAL
     assert L.mp3pcf_counts(None, None, None) == lib.EINVAL
     assert L.mp3pcf_last_error(None) == b"null context"
+
+
+def test_a_plain_c99_caller_builds_and_runs(lib, orc, tmp_path):
+    """tests/c/abi_host.c includes only include/mp3pcf.h (compiled as strict C99, warnings as
+    errors) and links the library; its host-only calls agree with the oracle's edge table."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    so = lib.lib_path()
+    exe = str(tmp_path / "abi_host")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "c", "abi_host.c"),
+                    "-L", os.path.dirname(so), "-l:" + os.path.basename(so),
+                    "-Wl,-rpath," + os.path.dirname(so), "-o", exe], check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    rows = [r.split() for r in out if r.strip()]
+    e = np.array([float(r[1]) for r in rows])
+    e2 = np.array([int(r[2]) for r in rows])
+    oe, oe2 = orc.edges(orc.Setup(n_bins=20, theta_min=0.5, theta_max=120.0, n_max=30))
+    np.testing.assert_array_equal(e2, oe2)
+    np.testing.assert_array_equal(e, oe)
