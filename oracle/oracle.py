@@ -156,7 +156,7 @@ def grid_catalog(cat, origin, pixel_q: int, npx: int, npy: int, n_z: int = 1):
                    None if n_z == 1 else (k // (npx * npy)).astype(np.uint8), 0.0, cat.quantum)
 
 
-def combined_moments(s: Setup, cat, levels, centres: Optional[np.ndarray] = None):
+def combined_moments(s: Setup, cat, levels, centres: Optional[np.ndarray] = None, extent=None):
     """The moments of the combined estimator (Sec. 3.3): level l = (b_start, pixel_q) of levels
     covers the radial bins [b_start_l, b_start_{l+1}) (the last up to n_bins) with the pixel
     catalog of side pixel_q quanta on the grid whose origin is the catalog's lower corner
@@ -164,8 +164,9 @@ def combined_moments(s: Setup, cat, levels, centres: Optional[np.ndarray] = None
     about the pixel centre (G_n^Delta at its pixel, with no division by the galaxies per pixel:
     the reading under which Eq. CombinedEstimatorRegridding's two lines agree). The bins below the
     first level keep the galaxies' discrete moments (Eq. Gn_disc). A galaxy whose pixel has no
-    weight gets zeros. Plain steps: all moments of the galaxies and of every pixel catalog, then a
-    copy of the levels' bins."""
+    weight gets zeros. extent = (x0, y0, x1, y1) in quanta (a fixed patch extent, x1 and y1 the
+    largest positions) replaces the catalog's bounding box when given. Plain steps: all moments
+    of the galaxies and of every pixel catalog, then a copy of the levels' bins."""
     if centres is None:
         centres = np.arange(cat.n, dtype=np.int64)
     centres = np.asarray(centres, dtype=np.int64)
@@ -173,12 +174,15 @@ def combined_moments(s: Setup, cat, levels, centres: Optional[np.ndarray] = None
     xq = np.asarray(cat.xq, np.int64)
     yq = np.asarray(cat.yq, np.int64)
     z = np.zeros(cat.n, np.int64) if cat.zbin is None else np.asarray(cat.zbin, np.int64)
-    x0, y0 = int(xq.min()), int(yq.min())
+    if extent is None:
+        x0, y0, x1, y1 = int(xq.min()), int(yq.min()), int(xq.max()), int(yq.max())
+    else:
+        x0, y0, x1, y1 = (int(v) for v in extent)
     for l, (b0, q) in enumerate(levels):
         b1 = int(levels[l + 1][0]) if l + 1 < len(levels) else s.n_bins
         q = int(q)
-        npx = (int(xq.max()) - x0) // q + 1
-        npy = (int(yq.max()) - y0) // q + 1
+        npx = (x1 - x0) // q + 1
+        npy = (y1 - y0) // q + 1
         pix = grid_catalog(cat, (x0, y0), q, npx, npy, s.n_z)
         Gp, Wp = moments(s, pix)
         # the catalog index of each centre's pixel among the non-empty pixels ((z, iy, ix) order)

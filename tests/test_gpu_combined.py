@@ -78,6 +78,42 @@ def test_all_bins_on_the_grid_and_empty_catalogs(gpu, orc):
         assert not ups.abs().any() and not norm.abs().any()
 
 
+def test_fixed_extent_and_context_reuse(gpu, orc):
+    """With a fixed extent the grids start at its lower corner (the oracle given the same extent);
+    and one context running catalogs and levels of different sizes in turn gives, bit for bit,
+    what a fresh context gives for each (FP64, whose sums run in a fixed order)."""
+    cat = _catalog(1)
+    s = orc.Setup(**SETUP)
+    ext = (int(cat.xq.min()) - 3001, int(cat.yq.min()) - 1777, int(cat.xq.max()) + 999, int(cat.yq.max()) + 5)
+    G0, W0 = orc.combined_moments(s, cat, LEVELS, extent=ext)
+    G1, _ = orc.combined_moments(s, cat, LEVELS)
+    assert rel_err(G1[:, :, 2:], G0[:, :, 2:]) > 1e-3  # the shifted grids change the grid bins
+    dev = gpu.catalog_to_device(cat)
+    with gpu.Estimator(**SETUP, precision="fp64") as est:
+        est.set_extent(ext)
+        est.accumulate_moments_combined(*dev[:5], levels=LEVELS)
+        G, W = est.moments()
+    assert rel_err(G.cpu().numpy(), G0) < 1e-10 and rel_err(W.cpu().numpy(), W0) < 1e-10
+
+    small = synth.make_catalog(800, 20.0, 5, field="noise", weights="uniform")
+    big = synth.make_catalog(6000, 40.0, 6, field="lognormal", weights="uniform", ngrid=512)
+    seq = [(big, LEVELS), (small, [(1, Q)]), (big, [(3, 2 * Q)]), (small, LEVELS), (big, LEVELS)]
+
+    def run(est, c, lv):
+        d = gpu.catalog_to_device(c)
+        est.accumulate_moments_combined(*d[:5], levels=lv)
+        G, _ = est.moments()
+        ups, norm = est.contract()
+        return G.cpu().numpy(), ups.cpu().numpy(), norm.cpu().numpy()
+
+    with gpu.Estimator(**SETUP, precision="fp64") as est:
+        reused = [run(est, c, lv) for c, lv in seq]
+    for (c, lv), got in zip(seq, reused):
+        with gpu.Estimator(**SETUP, precision="fp64") as fresh:
+            want = run(fresh, c, lv)
+        assert all(np.array_equal(a, b) for a, b in zip(got, want)), lv
+
+
 def test_combined_arguments_are_checked(gpu):
     from paper_2309_08601_gb300 import native
     cat = _catalog(1)
