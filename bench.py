@@ -45,7 +45,7 @@ HBM_PEAK_GBS = _measured_hbm_gbs()
 # workload: ncu capture at 50 000 galaxies (profiles/moments_kernel_lognormal_50k.md) scaled to
 # 200 000 centres (the traffic is the G/W write, proportional to the number of centres).
 # Set to None whenever the kernel changes until it is captured again.
-MOMENTS_TRAFFIC_BYTES = 4 * (124.219136e6 + 1053.288e6)
+MOMENTS_TRAFFIC_BYTES = 4 * (125.665792e6 + 1052.680e6)
 # DRAM bytes per launch of the tensor-core contraction (BF16x3) at lognormal_200k: ncu capture
 # at 50 000 galaxies (profiles/contract_tc_bf16x3_lognormal_50k.md) scaled to 200 000 centres
 # (the traffic is the moment stream, proportional to the centres). None whenever it changes.

@@ -9,9 +9,11 @@
 //    candidate stream (prefix sums of their lengths) and split evenly between the warps.
 //  * The bin is processed in rounds. Produce: each warp tests SCR candidates of its share,
 //    exactly on the integer squared separation, and compacts the members (ballot + popc) into
-//    its region of a shared-memory chunk, storing z = (dx + i dy)/r, its powers z^2..z^P, and
-//    w gamma_1, w gamma_2, w. The candidates' positions and payloads were copied into shared
-//    memory by cp.async one round earlier, so this phase does not wait on memory.
+//    its region of a shared-memory chunk, storing z = (dx + i dy)/r, its powers z^2..z^P, the
+//    pair (w gamma_1, w gamma_2) as one 8-byte record (one shared load per member where two
+//    4-byte loads cost 2.6 % of the kernel's time) and w. The candidates' positions and
+//    payloads were copied into shared memory by cp.async one round earlier, so this phase does
+//    not wait on memory.
 //    Consume: warp p owns the orders m = p, p + P, p + 2P, ... (all warps do the same work),
 //    walks every member of the chunk, steps through its orders with the three-term recurrence
 //    c_{j+1} = 2 cos(P phi) c_j - c_{j-1} (two FMAs per order) and accumulates
@@ -71,7 +73,8 @@ struct MomPlan {
 template <typename T, int P, int SCR>
 struct MomSmem {
     cx<T> zp[P][P * SCR];     // z^1 .. z^P of each member
-    T a[P * SCR], b[P * SCR], w[P * SCR];
+    cx<T> ab[P * SCR];        // (w gamma_1, w gamma_2) of each member
+    T w[P * SCR];
     int2 spos[P][SCR];        // staged candidate positions (cp.async, one round ahead)
     Pay<T> spay[P][SCR];      // staged candidate payloads
     int2 seg[2 * kMaxRows];   // (first sorted index, count) of the current bin's ranges
@@ -212,7 +215,7 @@ __global__ void __launch_bounds__(MomPlan<T, NMAX>::NT, MomPlan<T, NMAX>::MINB) 
     const bool lastAB = warp + (NABM - 1) * P <= NMAX + 3;
     const int zsel = warp > 0 ? warp - 1 : 0;
     const uint32_t zp_base = smem_u32(&s.zp[0][0]);
-    const uint32_t a_base = smem_u32(&s.a[0]), b_base = smem_u32(&s.b[0]), w_base = smem_u32(&s.w[0]);
+    const uint32_t ab_base = smem_u32(&s.ab[0]), w_base = smem_u32(&s.w[0]);
     const uint32_t aP = zp_base + (uint32_t)((P - 1) * CH * sizeof(cx<T>));
     const uint32_t aq = zp_base + (uint32_t)(zsel * CH * sizeof(cx<T>));
     int2* my_pos = s.spos[warp];
@@ -359,8 +362,7 @@ __global__ void __launch_bounds__(MomPlan<T, NMAX>::NT, MomPlan<T, NMAX>::MINB) 
                         }
                         if (in) {
                             const Pay<T> py = my_pay[u * 32 + lane];
-                            s.a[slot] = py.a;
-                            s.b[slot] = py.b;
+                            s.ab[slot] = cx<T>{py.a, py.b};
                             s.w[slot] = py.w;
                         }
                         mycnt += __popc(m);
@@ -380,8 +382,8 @@ __global__ void __launch_bounds__(MomPlan<T, NMAX>::NT, MomPlan<T, NMAX>::MINB) 
                         for (int e = e0 + lane; e < e0 + cnt; e += 32) {
                             const cx<T> zP = lds_cx(aP + e * (uint32_t)sizeof(cx<T>), T(0));
                             const cx<T> zq = lds_cx(aq + e * (uint32_t)sizeof(cx<T>), T(0));
-                            const T av = lds_r(a_base + e * (uint32_t)sizeof(T), T(0));
-                            const T bv = lds_r(b_base + e * (uint32_t)sizeof(T), T(0));
+                            const cx<T> abv = lds_cx(ab_base + e * (uint32_t)sizeof(cx<T>), T(0));
+                            const T av = abv.x, bv = abv.y;
                             const T wv = lds_r(w_base + e * (uint32_t)sizeof(T), T(0));
                             // orders m_j = warp + j P. With |z| = 1, z^{m+P} + z^{m-P} =
                             // 2 cos(P phi) z^m, so c_{j+1} = kappa c_j - c_{j-1}, kappa = 2 Re(z^P),
