@@ -85,3 +85,25 @@ def test_galaxies_beyond_the_cut_off_do_not_count(orc):
     a = orc.map3_direct(cat, [[OFF, OFF]], [1.0, 2.0, 3.0])
     b = orc.map3_direct(both, [[OFF, OFF]], [1.0, 2.0, 3.0])
     assert np.array_equal(a, b)
+
+
+def test_aperture_grid_and_the_mean_over_apertures():
+    """api.aperture_centres keeps every aperture rcut_factor * max(theta) inside the bounding box
+    on a grid of the smallest radius; api.map3_from_direct averages numerator / denominator over
+    the apertures with a non-zero denominator."""
+    from paper_2309_08601_gb300 import api
+    q = 2.0 ** -13
+    xq = np.array([0, 800_000, 0, 800_000], dtype=np.int32)  # a 97.66' square
+    yq = np.array([0, 0, 800_000, 800_000], dtype=np.int32)
+    th = [[2.0, 2.0, 2.0], [4.0, 4.0, 8.0]]
+    c = api.aperture_centres(xq, yq, q, th)
+    side = 800_000 * q
+    assert c.shape[1] == 2 and len(c) > 0
+    assert (c >= 32.0 - 1e-9).all() and (c <= side - 32.0 + 1e-9).all()
+    steps = np.diff(np.unique(c[:, 0]))
+    assert np.allclose(steps, 2.0)
+    assert api.aperture_centres(xq[:2], yq[:2], q, th).shape == (0, 2)  # no room inside the margins
+    out = np.zeros((3, 2, 2))  # [aperture][radii triple][numerator, denominator]
+    out[..., 0] = [[1.0, 2.0], [2.0, 0.0], [3.0, 4.0]]
+    out[..., 1] = [[1.0, 2.0], [2.0, 0.0], [0.0, 4.0]]  # zero denominators are left out
+    np.testing.assert_allclose(api.map3_from_direct(out), [1.0, 1.0])
