@@ -839,6 +839,7 @@ static mp3pcf_status combined_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq, c
         int cnt = 0;
         MP3_CK(cudaMemcpyAsync(&cnt, rank + npix, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
         MP3_CK(cudaStreamSynchronize(ctx->st));
+        if (cnt > INT_MAX / 2) return fail(ctx, MP3PCF_EINVAL, "a grid level has more than 2^30 non-empty pixels");
         // the pixel catalog's moments of this level's bins
         int64_t before[6];
         for (int i = 0; i < 6; ++i) before[i] = sub->launches[i];
