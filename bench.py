@@ -46,10 +46,11 @@ HBM_PEAK_GBS = _measured_hbm_gbs()
 # 200 000 centres (the traffic is the G/W write, proportional to the number of centres).
 # Set to None whenever the kernel changes until it is captured again.
 MOMENTS_TRAFFIC_BYTES = 4 * (125.665792e6 + 1052.680e6)
-# DRAM bytes per launch of the tensor-core contraction (BF16x3) at lognormal_200k: ncu capture
-# at 50 000 galaxies (profiles/contract_tc_bf16x3_lognormal_50k.md) scaled to 200 000 centres
-# (the traffic is the moment stream, proportional to the centres). None whenever it changes.
-CONTRACT_TRAFFIC_BYTES = 4 * (1.066084e9 + 9.231360e6)
+# DRAM bytes per launch of the tensor-core contraction (BF16x3) at lognormal_200k, from an ncu
+# capture scaled by the centres, or None. None now: the kernel has since been changed to read only
+# each Z1's centre range (the same work at one z-bin); its last capture, 4 x (1.066084e9 +
+# 9.231360e6) bytes, is kept in profiles/contract_tc_bf16x3_lognormal_50k.md.
+CONTRACT_TRAFFIC_BYTES = None
 
 
 def flops_per_pair(n_max: int) -> int:
