@@ -951,6 +951,10 @@ mp3pcf_status mp3pcf_contract_multipoles(mp3pcf_ctx* ctx, double* d_upsilon, dou
         ctx->launches[ST_CONTRACT] += 3;
         MP3_CK(launch_contract_tc(a, tf32, ctx->n_sm, ctx->ccoef.as<float4>(), errw, &splits, false,
                                   c.contract_slices, ctx->inject_wait_timeout ? 1 : 0, ctx->st));
+        if (c.exclude_degenerate) {
+            ctx->launches[ST_CONTRACT] += 1;
+            MP3_CK(launch_contract_diag(a, ctx->st));
+        }
         MP3_CK(launch_contract_reduce(ctx->partial.as<double>(), splits, nz, nb, c.n_max, d_upsilon, d_norm,
                                       ctx->st));
         if (c.exclude_degenerate) return degenerate_t<float>(ctx, d_upsilon, d_norm);
@@ -1033,7 +1037,7 @@ mp3pcf_status mp3pcf_to_gamma(mp3pcf_ctx* ctx, const double* d_gamma_n, int32_t 
 mp3pcf_status mp3pcf_to_map3(mp3pcf_ctx* ctx, const double* d_gamma_cen, int64_t n_ap,
                              const double* d_theta_ap, double* d_corr, double* d_m8)
 {
-    if (!ctx || !d_gamma_cen || n_ap < 0 || n_ap > 65535 || (n_ap > 0 && !d_theta_ap))
+    if (!ctx || !d_gamma_cen || n_ap < 0 || n_ap > 65535 || (n_ap > 0 && (!d_theta_ap || (!d_corr && !d_m8))))
         return fail(ctx, MP3PCF_EINVAL, "bad argument");
     ctx->err.clear();
     if (n_ap == 0) return MP3PCF_OK;

@@ -125,6 +125,9 @@ cudaError_t launch_contract_f64(const ContractArgs<double>& a, cudaStream_t st);
 cudaError_t launch_contract_tc(const ContractArgs<float>& a, bool tf32, int n_sm, float4* coef,
                                unsigned long long* err, int* splits, bool plan_only, int fixed_slices,
                                int skip_copies, cudaStream_t st);
+// exclude_degenerate with a tensor-core form: recomputes the b1 = b2 slice partials of the
+// Z-triplets with Z2 = Z3 in FP64 (a.partial, a.splits as filled by launch_contract_tc)
+cudaError_t launch_contract_diag(const ContractArgs<float>& a, cudaStream_t st);
 cudaError_t launch_contract_reduce(const double* partial, int splits, int nz, int nb, int n_max,
                                    double* ups, double* norm, cudaStream_t st);
 

@@ -147,6 +147,96 @@ __global__ void contract_reduce_kernel(const double* __restrict__ partial, int s
     }
 }
 
+// exclude_degenerate with the tensor-core forms: the b1 = b2 blocks of the Z-triplets with
+// Z2 = Z3, the only blocks from which the j = k share is removed, summed again over the centres
+// with the FP32 moments' products formed and accumulated in FP64. The j = k share is the largest
+// part of these blocks when a bin holds few neighbours, so removing it from a split-BF16 sum would
+// leave that sum's rounding of the removed share in the small remainder. Block (diagonal group,
+// slice): lanes over the bins, warps over the slice's centres, a fixed-order reduction over the
+// warps; the result replaces the tensor-core slice partial of the same (slice, group, b, b), so the
+// slice reduction that follows adds it like any other partial.
+constexpr int kDiagWarps = 8;
+
+__global__ void __launch_bounds__(kDiagWarps * 32) contract_diag_kernel(const ContractArgs<float> a)
+{
+    const int nb = a.nb, nz = a.nz, n_max = a.n_max;
+    const int per_zt = groups_per_zt(n_max);
+    const int loc = blockIdx.x % per_zt, zz = blockIdx.x / per_zt;  // zz = z1 * nz + z2, z3 = z2
+    const int z1 = zz / nz, z2 = zz % nz;
+    const int zt = (z1 * nz + z2) * nz + z2;
+    const int g = zt * per_zt + loc, sl = blockIdx.y;
+    int kind, n;
+    if (loc < 4 * (n_max + 1)) {
+        kind = loc / (n_max + 1);
+        n = loc % (n_max + 1);
+    } else {
+        kind = 4;
+        n = loc - 4 * (n_max + 1);
+    }
+    int mx, my;
+    bool xconj = false, yconj = false;
+    switch (kind) {
+        case 0: mx = n - 3; my = -n - 3; break;
+        case 1: mx = n - 1; my = -n - 1; break;
+        case 2: mx = -n - 1; my = -n - 3; xconj = true; break;
+        case 3: mx = n - 3; my = n - 1; yconj = true; break;
+        default: mx = n; my = n; yconj = true; break;
+    }
+    const int off = kind < 4 ? n_max + 3 : 0;
+    const int nbp = nb_pad(nb);
+    const size_t plane = (size_t)a.n_centres * nz * nbp;
+    const cx<float>* src = kind < 4 ? a.G : a.W;
+    const int zc0 = a.zrange ? a.zrange[z1] : 0, zc1 = a.zrange ? a.zrange[z1 + 1] : a.n_centres;
+    const int per = (zc1 - zc0 + a.splits - 1) / a.splits;
+    const int c0 = min(zc1, zc0 + sl * per), c1 = min(zc1, c0 + per);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ double red[kDiagWarps][kMaxBins][2];
+    for (int b0 = 0; b0 < nb; b0 += 32) {
+        const int b = b0 + lane;
+        double sr = 0.0, si = 0.0;
+        if (b < nb) {
+            for (int c = c0 + warp; c < c1; c += kDiagWarps) {
+                const int d = a.centre_idx[c];
+                if ((a.zs ? (int)a.zs[d] : 0) != z1) continue;
+                const Pay<float> pv = a.pay[d];
+                cx<double> coef;
+                if (kind == 4) coef = cx<double>{(double)pv.w, 0.0};
+                else if (kind == 1) coef = cx<double>{-(double)pv.a, (double)pv.b};
+                else coef = cx<double>{-(double)pv.a, -(double)pv.b};
+                const cx<float> xf = src[(size_t)(mx + off) * plane + ((size_t)c * nz + z2) * nbp + b];
+                const cx<float> yf = src[(size_t)(my + off) * plane + ((size_t)c * nz + z2) * nbp + b];
+                cx<double> x{(double)xf.x, xconj ? -(double)xf.y : (double)xf.y};
+                const cx<double> y{(double)yf.x, yconj ? -(double)yf.y : (double)yf.y};
+                x = cmul(coef, x);
+                sr += x.x * y.x - x.y * y.y;
+                si += x.x * y.y + x.y * y.x;
+            }
+            red[warp][b][0] = sr;
+            red[warp][b][1] = si;
+        }
+    }
+    __syncthreads();
+    const int groups = nz * nz * nz * per_zt, nbb = nb * nb;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        double tr = 0.0, ti = 0.0;
+        for (int w = 0; w < kDiagWarps; ++w) {
+            tr += red[w][b][0];
+            ti += red[w][b][1];
+        }
+        double* dst = a.partial + 2 * (((size_t)sl * groups + g) * nbb + (size_t)b * nb + b);
+        dst[0] = tr;
+        dst[1] = ti;
+    }
+}
+
+cudaError_t launch_contract_diag(const ContractArgs<float>& a, cudaStream_t st)
+{
+    if (a.splits < 1 || a.n_centres <= 0) return cudaSuccess;
+    dim3 grid(a.nz * a.nz * groups_per_zt(a.n_max), a.splits);
+    contract_diag_kernel<<<grid, kDiagWarps * 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t launch_contract_t(const ContractArgs<T>& a, cudaStream_t st)
 {

@@ -32,13 +32,13 @@ def _oracle(orc, cat, setup, theta):
     return orc.pipeline(s, cat, theta)
 
 
-@pytest.mark.parametrize("precision,tol,tol_gamma", [("fp64", 1e-10, 1e-10), ("bf16x3", 1e-4, 1e-3),
-                                                     ("fp32", 1e-4, 1e-3)])
+@pytest.mark.parametrize("precision,tol,tol_gamma", [("fp64", 1e-10, 1e-10), ("bf16x3", 1e-4, 1e-4),
+                                                     ("tf32x3", 1e-4, 1e-4), ("fp32", 1e-4, 1e-4)])
 def test_exclude_degenerate_matches_oracle(gpu, orc, noise2k, precision, tol, tol_gamma):
-    """Upsilon and N to the FP32 tolerance; Gamma to 1e-3 in the FP32 forms: without the j = k
-    terms the mode-coupling systems lose their diagonal contribution and the solve amplifies the
-    contraction's relative error ~20x on this noise catalog (with j = k included the same forms
-    meet 1e-4 on Gamma, test_gpu_parity.py)."""
+    """Every output within the reduced-precision tolerance. Without the j = k terms the b1 = b2
+    blocks are small remainders of larger sums and the small-bin systems are poorly conditioned,
+    so the tensor-core forms recompute those blocks in FP64 from the FP32 moments before the j = k
+    share is removed (with split-BF16 blocks Gamma^cen was 1.04e-4 off on this catalog)."""
     setup = dict(S0, exclude_degenerate=1)
     r = _oracle(orc, noise2k, setup, TH0)
     g = _run(gpu, noise2k, setup, precision, TH0)
