@@ -304,6 +304,53 @@ def test_multipoles_converge_to_binned_triplet_sums(orc):
     assert errs_u[-1] < 0.12 * errs_u[0] and errs_n[-1] < 0.12 * errs_n[0]
 
 
+def test_to_gamma_converges_to_binned_triplet_sums(orc):
+    """orc_to_gamma against the brute-force angular bins, in both projections (Sec. 3.4, the
+    multipole series of Gamma; Sec. 2.3, Eqs. X2Centroid0-3; the binned sums of Sec. 2.4).
+
+    Fed the multipoles Upsilon_n themselves (extended to n < 0 by the edge correction with a unit
+    mode-coupling matrix, i.e. N_0 = 1 and N_m = 0 otherwise), to_gamma returns
+    sum_n Upsilon_n e^{i n phi}, which tends to 2 pi times the triplet density in phi; its average
+    over an angular bin of width 2 pi / K then tends to K times the brute-force sum of that bin.
+    The averages are taken over 512 points of to_gamma's own phi grid per bin. In the centroid
+    projection the brute force applies each triplet's own factor at its exact radii, to_gamma
+    the factor at the radial nodes, so narrow radial bins are used and only b1 != b2 blocks are
+    compared (for b1 = b2 the exact factor of a nearly isosceles triplet flips sign near
+    phi = pi). A flipped exponent (Gamma(-phi) returned for Gamma(phi)) does not converge."""
+    rng = np.random.default_rng(7)
+    n = 400
+    xy = rng.uniform(0, 10, (n, 2))
+    g = rng.normal(0, 0.3, n) + 1j * rng.normal(0, 0.3, n)
+    cat = hand_catalog(xy, g, rng.uniform(0.5, 1.5, n))
+    K, S = 6, 512
+    setup = dict(n_bins=3, theta_min=2.0, theta_max=2.1)
+    ref = orc.brute(orc.Setup(**setup, n_max=2), cat, n_phib=K)
+    off = ~np.eye(setup["n_bins"], dtype=bool)
+
+    def bin_avg(out):
+        return out.reshape(out.shape[:-1] + (K, S)).mean(-1) / K
+
+    ex, ec, eflip = [], [], []
+    for nmax in (10, 40, 160, 640):
+        s = orc.Setup(**setup, n_max=nmax)
+        G, W = orc.moments(s, cat)
+        ups, norm = orc.contract(s, cat, G, W)
+        unit = np.zeros_like(norm)
+        unit[:, 0] = 1.0
+        ext, ns = orc.edge_correct(s, ups, unit)
+        assert ns == 0
+        sp = orc.Setup(**setup, n_max=nmax, n_phi=K * S)
+        out0, out1 = orc.to_gamma(sp, ext, 0), orc.to_gamma(sp, ext, 1)
+        # degenerate triplets (j = k) sit at phi = 0, a bin edge: merge the bins around it
+        ex.append(rel_err(_merge0(bin_avg(out0)), _merge0(ref.ups_b)))
+        eflip.append(rel_err(_merge0(bin_avg(out0[..., ::-1])), _merge0(ref.ups_b)))
+        ec.append(rel_err(bin_avg(out1)[:, :, off], ref.upsc_b[:, :, off]))
+    assert all(a > b for a, b in zip(ex, ex[1:])), ex
+    assert all(a > b for a, b in zip(ec, ec[1:])), ec
+    assert ex[-1] < 0.25 * ex[0] and ec[-1] < 0.35 * ec[0], (ex, ec)
+    assert min(eflip) > 10 * ex[-1], eflip
+
+
 # ------------------------------------- P6: aperture filters against their defining integrals
 
 def _F_by_integration(mu, t1, t2, phi, th, n=801):
