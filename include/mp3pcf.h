@@ -162,7 +162,8 @@ mp3pcf_status mp3pcf_to_gamma(mp3pcf_ctx* ctx, const double* d_gamma_n, int32_t 
  * (arcmin, device). Outputs (device): d_corr [n_z^3][n_ap][4] complex double
  * (<M^3>, <M^* M^2>, <M M^* M>, <M^2 M^*>) and d_m8 [n_z^3][n_ap][8] double, the eight real
  * measures of Eqs. MapTrafo8_1-8 in the order Map^3, <Mx Map Map>, <Map Mx Map>,
- * <Map Map Mx>, <Map Mx Mx>, <Mx Map Mx>, <Mx Mx Map>, Mx^3. Either output may be NULL. */
+ * <Map Map Mx>, <Map Mx Mx>, <Mx Map Mx>, <Mx Mx Map>, Mx^3. Either output may be NULL, not both
+ * (EINVAL when n_ap > 0). */
 mp3pcf_status mp3pcf_to_map3(mp3pcf_ctx* ctx, const double* d_gamma_cen, int64_t n_ap,
                              const double* d_theta_ap, double* d_corr, double* d_m8);
 
@@ -323,6 +324,14 @@ mp3pcf_status mp3pcf_moments_adjoint(mp3pcf_ctx* ctx, const double* d_grad_upsil
 mp3pcf_status mp3pcf_set_timing(mp3pcf_ctx* ctx, int32_t on);
 mp3pcf_status mp3pcf_stage_times(mp3pcf_ctx* ctx, double* h_ms, int64_t* h_launches, int32_t reset);
 
+/* Measurement service for rooflines (the paper has no counterpart). Runs, on the current device
+ * and `stream`, a probe that keeps every SM busy with independent chains of one arithmetic
+ * instruction: kind 0 FP32 FMA, 1 packed two-lane FP32 FMA (sm_100 and later), 2 FP64 FMA.
+ * Returns the best of three timed launches (after one warm-up) in *h_flops_per_s (2 flops per
+ * FMA) and an estimate of the SM clock during the probe in *h_sm_mhz (may be NULL). Allocates
+ * and frees two small device buffers and synchronises the stream. EINVAL for another kind. */
+mp3pcf_status mp3pcf_measure_peak(int32_t kind, void* stream, double* h_flops_per_s, double* h_sm_mhz);
+
 /* Allocation-free form of mp3pcf_to_map3 (the paper has no counterpart: it is a service of this
  * library). For callers that may not allocate device memory, e.g. a plugin inside a host
  * application that owns all device memory through its own pool, or a service held to a fixed
@@ -333,8 +342,11 @@ mp3pcf_status mp3pcf_stage_times(mp3pcf_ctx* ctx, double* h_ms, int64_t* h_launc
  * library until the process exits. It limits n_z^3 * n_ap to at most 255; larger requests
  * return EINVAL and enqueue nothing. Every call shares that array: calls whose work overlaps on
  * the GPU (two streams, or two host threads on one device) race and must be ordered by the
- * caller. The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * caller. The array's device address is looked up (cudaGetSymbolAddress) by every call made
+ * outside stream capture and cached per CUDA context; a call made while `stream` is capturing
+ * uses the cached address of the current context, so make a first call in that context outside
+ * capture (again after cudaDeviceReset, which reloads the library's module), or the call
+ * returns ECUDA. Either output may be NULL, not both.
  * Returns EINVAL for a bad configuration or argument, ECUDA if a CUDA call fails. */
 mp3pcf_status mp3pcf_to_map3_noalloc(const mp3pcf_config* cfg, void* stream,
                                      const double* d_gamma_cen, int64_t n_ap,

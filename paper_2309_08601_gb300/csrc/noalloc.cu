@@ -33,24 +33,63 @@ __global__ void noalloc_write_tables(const NoAllocTables t, int nb, double* dst)
     for (int i = threadIdx.x; i < nb; i += blockDim.x) dst[kMaxBins + 1 + i] = t.nodes[i];
 }
 
-// device address of the scratch array, looked up once per device
-static std::mutex g_noalloc_mu;
-static double* g_noalloc_ptr[64] = {nullptr};
+// Device address of the scratch array. It belongs to the module the runtime loaded into the
+// current context, so it is cached per context (the driver's context handle, obtained through the
+// runtime's driver entry point, needs no link to libcuda). Outside stream capture every call looks
+// the address up again and refreshes the cache: after cudaDeviceReset the module is loaded anew
+// and the array may have moved, and a non-primary context has its own copy. During capture the
+// lookup (which may load the module) is not attempted and the cached address of the current
+// context is used; without one the call fails.
+typedef int (*CtxGetCurrentFn)(void**);
 
-static cudaError_t noalloc_scratch(double** out)
+static std::mutex g_noalloc_mu;
+constexpr int kNoAllocCtxSlots = 64;
+static void* g_noalloc_ctx[kNoAllocCtxSlots] = {nullptr};
+static double* g_noalloc_ptr[kNoAllocCtxSlots] = {nullptr};
+static int g_noalloc_next = 0;
+
+static void* current_context()
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    static CtxGetCurrentFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<CtxGetCurrentFn>(f);
+    }();
+    void* ctx = nullptr;
+    if (!fn || fn(&ctx) != 0) return nullptr;
+    return ctx;
+}
+
+static cudaError_t noalloc_scratch(cudaStream_t st, double** out)
+{
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cap);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    void* ctx = current_context();
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    int slot = -1;
+    for (int i = 0; i < kNoAllocCtxSlots; ++i)
+        if (g_noalloc_ptr[i] && g_noalloc_ctx[i] == ctx) slot = i;
+    if (cap != cudaStreamCaptureStatusNone) {
+        if (slot < 0 || !ctx) return cudaErrorStreamCaptureUnsupported;
+        *out = g_noalloc_ptr[slot];
+        return cudaSuccess;
     }
-    *out = g_noalloc_ptr[dev];
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    if (ctx) {
+        if (slot < 0) {
+            slot = g_noalloc_next;
+            g_noalloc_next = (g_noalloc_next + 1) % kNoAllocCtxSlots;
+        }
+        g_noalloc_ctx[slot] = ctx;
+        g_noalloc_ptr[slot] = static_cast<double*>(p);
+    }
+    *out = static_cast<double*>(p);
     return cudaSuccess;
 }
 
@@ -65,7 +104,7 @@ extern "C" mp3pcf_status mp3pcf_to_map3_noalloc(const mp3pcf_config* cfg, void* 
 {
     NoAllocTables t;
     if (!cfg || mp3pcf_bin_edges(cfg, t.e, nullptr) != MP3PCF_OK) return MP3PCF_EINVAL;
-    if (!d_gamma_cen || n_ap < 0 || (n_ap > 0 && !d_theta_ap)) return MP3PCF_EINVAL;
+    if (!d_gamma_cen || n_ap < 0 || (n_ap > 0 && (!d_theta_ap || (!d_corr && !d_m8)))) return MP3PCF_EINVAL;
     const int nb = cfg->n_bins;
     const long long jobs = (long long)cfg->n_z * cfg->n_z * cfg->n_z * n_ap;
     if (jobs > (long long)kNoAllocMaxJobs) return MP3PCF_EINVAL;  // beyond the static scratch
@@ -73,8 +112,8 @@ extern "C" mp3pcf_status mp3pcf_to_map3_noalloc(const mp3pcf_config* cfg, void* 
     for (int b = 0; b < nb; ++b)
         t.nodes[b] = cfg->radial_nodes ? sqrt(t.e[b] * t.e[b + 1]) : 0.5 * (t.e[b] + t.e[b + 1]);
     double* scratch = nullptr;
-    if (noalloc_scratch(&scratch) != cudaSuccess) return MP3PCF_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
+    if (noalloc_scratch(st, &scratch) != cudaSuccess) return MP3PCF_ECUDA;
     noalloc_write_tables<<<1, 128, 0, st>>>(t, nb, scratch);
     if (cudaGetLastError() != cudaSuccess) return MP3PCF_ECUDA;
     PostArgs p;
