@@ -48,6 +48,7 @@ SIGNATURES = {
     "mp3pcf_set_timing": ([P, I32], C.c_int),
     "mp3pcf_stage_times": ([P, P, P, I32], C.c_int),
     "mp3pcf_to_map3_noalloc": ([P, P, P, I64, P, P, P], C.c_int),
+    "mp3pcf_measure_peak": ([I32, P, P, P], C.c_int),
     "mp3pcf_to_map3_adjoint": ([P, I64, P, P, P, P], C.c_int),
     "mp3pcf_to_gamma_adjoint": ([P, I32, P, P], C.c_int),
     "mp3pcf_edge_correct_adjoint": ([P, P, P, P, P, P], C.c_int),
