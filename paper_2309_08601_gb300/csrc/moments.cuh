@@ -16,9 +16,10 @@
 //    not wait on memory.
 //    Consume: warp p owns the orders m = p, p + P, p + 2P, ... (all warps do the same work),
 //    walks every member of the chunk, steps through its orders with the three-term recurrence
-//    c_{j+1} = 2 cos(P phi) c_j - c_{j-1} (two FMAs per order) and accumulates
-//    A_m = sum w gamma_1 z^m, B_m = sum w gamma_2 z^m (m <= n_max + 3) and W_m = sum w z^m
-//    (m <= 2 n_max) in registers. Two CTA barriers separate the phases; the next round's
+//    c_{j+1} = 2 cos(P phi) c_j - c_{j-1} and accumulates A_m = sum w gamma_1 z^m,
+//    B_m = sum w gamma_2 z^m (m <= n_max + 3) and W_m = sum w z^m (m <= 2 n_max) in registers;
+//    in FP32 the real and imaginary parts of each update go through one packed two-lane FMA
+//    (one instruction per order for the recurrence, and one each for A, B and W). Two CTA barriers separate the phases; the next round's
 //    candidate copies are issued between them, so they land while the warps consume.
 //  * At the end of a bin each warp reduce-scatters its per-lane sums across the warp and writes
 //    G_m = A_m + i B_m, G_{-m} = A_m^* + i B_m^* and W_m of its orders.
@@ -192,6 +193,130 @@ __device__ __forceinline__ void warp_reduce_scatter(T (&v)[N], int lane)
     }
 }
 
+// ------------------------------------------------------------------ per-lane accumulators
+//
+// A warp's sums of one (centre, z-bin, radial bin): A_m, B_m for its orders m = p + jP <= n_max + 3
+// and W_m for m = p + jP <= 2 n_max, each complex. MomAcc<T>::add takes one member and runs the
+// order recurrence c_{j+1} = kappa c_j - c_{j-1} (kappa = 2 cos(P phi)) over the warp's orders.
+// flatten() writes them as NAP scalars, in the order the reduce-scatter expects
+// (A_j.re, A_j.im, B_j.re, B_j.im for j < NABM, then W_j.re, W_j.im).
+template <typename T, int NABM, int NWM>
+struct MomAcc {
+    cx<T> a[NABM], b[NABM], w[NWM];
+
+    __device__ __forceinline__ void reset()
+    {
+#pragma unroll
+        for (int j = 0; j < NABM; ++j) a[j] = b[j] = cx<T>{T(0), T(0)};
+#pragma unroll
+        for (int j = 0; j < NWM; ++j) w[j] = cx<T>{T(0), T(0)};
+    }
+
+    __device__ __forceinline__ void add(T av, T bv, T wv, T kappa, cx<T> c0, cx<T> c1, bool lastAB, bool lastW)
+    {
+#pragma unroll
+        for (int j = 0; j < NWM; ++j) {
+            if (j < NABM && (j < NABM - 1 || lastAB)) {
+                a[j].x += av * c0.x;
+                a[j].y += av * c0.y;
+                b[j].x += bv * c0.x;
+                b[j].y += bv * c0.y;
+            }
+            if (j < NWM - 1 || lastW) {
+                w[j].x += wv * c0.x;
+                w[j].y += wv * c0.y;
+            }
+            if (j + 1 < NWM) {
+                const cx<T> c2{kappa * c1.x - c0.x, kappa * c1.y - c0.y};
+                c0 = c1;
+                c1 = c2;
+            }
+        }
+    }
+
+    template <int NAP>
+    __device__ __forceinline__ void flatten(T (&acc)[NAP]) const
+    {
+#pragma unroll
+        for (int j = 0; j < NABM; ++j) {
+            acc[4 * j + 0] = a[j].x;
+            acc[4 * j + 1] = a[j].y;
+            acc[4 * j + 2] = b[j].x;
+            acc[4 * j + 3] = b[j].y;
+        }
+#pragma unroll
+        for (int j = 0; j < NWM; ++j) {
+            acc[4 * NABM + 2 * j] = w[j].x;
+            acc[4 * NABM + 2 * j + 1] = w[j].y;
+        }
+#pragma unroll
+        for (int i = 4 * NABM + 2 * NWM; i < NAP; ++i) acc[i] = T(0);
+    }
+};
+
+// FP32: the real and imaginary parts of every sum and of the recurrence are updated together by
+// one packed two-lane FMA (__ffma2_rn, sm_100 and later), which halves the FMA instructions the
+// warp issues and leaves issue slots to the loads and the member loop. The recurrence's
+// subtraction is folded into the signs: the loop carries v_j = s_j c_j with
+// s_j = +1, +1, -1, -1, +1, +1, ... (period 4), for which v_{j+1} = (-1)^j kappa v_j + v_{j-1}
+// needs no negated addend; the sums of order slot j then hold s_j times their value and are
+// multiplied by s_j in flatten(). Negation is exact, so the results are bit-identical to the
+// scalar form above.
+template <int NABM, int NWM>
+struct MomAcc<float, NABM, NWM> {
+    float2 a[NABM], b[NABM], w[NWM];
+
+    __device__ __forceinline__ void reset()
+    {
+#pragma unroll
+        for (int j = 0; j < NABM; ++j) a[j] = b[j] = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int j = 0; j < NWM; ++j) w[j] = make_float2(0.0f, 0.0f);
+    }
+
+    __device__ __forceinline__ void add(float av, float bv, float wv, float kappa, cx<float> c0, cx<float> c1,
+                                        bool lastAB, bool lastW)
+    {
+        const float2 av2 = make_float2(av, av), bv2 = make_float2(bv, bv), wv2 = make_float2(wv, wv);
+        const float2 kp = make_float2(kappa, kappa), km = make_float2(-kappa, -kappa);
+        float2 v0 = make_float2(c0.x, c0.y), v1 = make_float2(c1.x, c1.y);
+#pragma unroll
+        for (int j = 0; j < NWM; ++j) {
+            if (j < NABM && (j < NABM - 1 || lastAB)) {
+                a[j] = __ffma2_rn(av2, v0, a[j]);
+                b[j] = __ffma2_rn(bv2, v0, b[j]);
+            }
+            if (j < NWM - 1 || lastW) w[j] = __ffma2_rn(wv2, v0, w[j]);
+            if (j + 1 < NWM) {
+                const float2 v2 = __ffma2_rn((j & 1) ? kp : km, v1, v0);
+                v0 = v1;
+                v1 = v2;
+            }
+        }
+    }
+
+    template <int NAP>
+    __device__ __forceinline__ void flatten(float (&acc)[NAP]) const
+    {
+#pragma unroll
+        for (int j = 0; j < NABM; ++j) {
+            const float sg = (j & 2) ? -1.0f : 1.0f;
+            acc[4 * j + 0] = sg * a[j].x;
+            acc[4 * j + 1] = sg * a[j].y;
+            acc[4 * j + 2] = sg * b[j].x;
+            acc[4 * j + 3] = sg * b[j].y;
+        }
+#pragma unroll
+        for (int j = 0; j < NWM; ++j) {
+            const float sg = (j & 2) ? -1.0f : 1.0f;
+            acc[4 * NABM + 2 * j] = sg * w[j].x;
+            acc[4 * NABM + 2 * j + 1] = sg * w[j].y;
+        }
+#pragma unroll
+        for (int i = 4 * NABM + 2 * NWM; i < NAP; ++i) acc[i] = 0.0f;
+    }
+};
+
 // ------------------------------------------------------------------ kernel
 
 template <typename T, int NMAX>
@@ -225,7 +350,7 @@ __global__ void __launch_bounds__(MomPlan<T, NMAX>::NT, MomPlan<T, NMAX>::MINB) 
     for (int i = tid; i <= nb; i += NT) s.e2q[i] = A.e2q[i];
     __syncthreads();
 
-    T acc[NAP];
+    MomAcc<T, NABM, NWM> macc;
     for (int c = blockIdx.x; c < A.n_centres; c += gridDim.x) {
         const int2 pc = A.pos[A.centre_idx[c]];
         const float fx = (float)((long long)pc.x - A.g.x0);
@@ -334,8 +459,7 @@ __global__ void __launch_bounds__(MomPlan<T, NMAX>::NT, MomPlan<T, NMAX>::MINB) 
                 };
                 int tb = tq0;
                 stage_candidates(tb);
-#pragma unroll
-                for (int i = 0; i < NAP; ++i) acc[i] = T(0);
+                macc.reset();
 
                 while (true) {
                     // ---- produce: this warp's staged candidates -> members in its region
@@ -387,32 +511,13 @@ __global__ void __launch_bounds__(MomPlan<T, NMAX>::NT, MomPlan<T, NMAX>::MINB) 
                             const T wv = lds_r(w_base + e * (uint32_t)sizeof(T), T(0));
                             // orders m_j = warp + j P. With |z| = 1, z^{m+P} + z^{m-P} =
                             // 2 cos(P phi) z^m, so c_{j+1} = kappa c_j - c_{j-1}, kappa = 2 Re(z^P),
-                            // real and imaginary parts alike (two FMAs per order). The recurrence
-                            // runs at most NWM - 2 steps, so its rounding error stays within a
-                            // few hundred ulp of the directly multiplied power.
+                            // real and imaginary parts alike. The recurrence runs at most NWM - 2
+                            // steps, so its rounding error stays within a few hundred ulp of the
+                            // directly multiplied power.
                             const T kappa = zP.x + zP.x;
-                            cx<T> c0 = warp == 0 ? cx<T>{T(1), T(0)} : zq;
-                            cx<T> c1 = warp == 0 ? zP : cmul(zq, zP);
-#pragma unroll
-                            for (int j = 0; j < NWM; ++j) {
-                                if (j < NABM) {
-                                    if (j < NABM - 1 || lastAB) {
-                                        acc[4 * j + 0] += av * c0.x;
-                                        acc[4 * j + 1] += av * c0.y;
-                                        acc[4 * j + 2] += bv * c0.x;
-                                        acc[4 * j + 3] += bv * c0.y;
-                                    }
-                                }
-                                if (j < NWM - 1 || lastW) {
-                                    acc[4 * NABM + 2 * j + 0] += wv * c0.x;
-                                    acc[4 * NABM + 2 * j + 1] += wv * c0.y;
-                                }
-                                if (j + 1 < NWM) {
-                                    const cx<T> c2{kappa * c1.x - c0.x, kappa * c1.y - c0.y};
-                                    c0 = c1;
-                                    c1 = c2;
-                                }
-                            }
+                            const cx<T> c0 = warp == 0 ? cx<T>{T(1), T(0)} : zq;
+                            const cx<T> c1 = warp == 0 ? zP : cmul(zq, zP);
+                            macc.add(av, bv, wv, kappa, c0, c1, lastAB, lastW);
                         }
                     }
                     __syncthreads();  // the chunk may be overwritten
@@ -420,6 +525,8 @@ __global__ void __launch_bounds__(MomPlan<T, NMAX>::NT, MomPlan<T, NMAX>::MINB) 
                 }
 
                 // ---- reduce over the warp and write G, W of (centre, Z, bin)
+                T acc[NAP];
+                macc.flatten(acc);
                 warp_reduce_scatter<T, NAP>(acc, lane);
                 constexpr int PER = NAP / 32;
                 T* st = stage + warp * NAP;
