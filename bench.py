@@ -2,10 +2,16 @@
 """Benchmark of the multipole shear-3PCF hot path on GB300.
 
 One step = the whole path on one catalog: cell sort, moments (stage a), multipole contraction
-(stage b), edge correction, Gamma^x and Gamma^cen, and the aperture measures. The workload is the
-200k-galaxy lognormal catalog on a 300'x300' patch (20 log bins 0.5'-120', n_max = 30, Map^3 at
-2', 4', 8', 16'). With N GPUs (torchrun) every rank measures its own catalog realisation
-(independent problems, weak scaling, no data-path collective).
+(stage b), edge correction, Gamma^x and Gamma^cen, and the aperture measures. The headline
+workload is the largest single-GPU configuration, the masked precision-form catalog: 10^6
+galaxies on a 600'x600' patch with circular holes covering 15 % of it, lognormal
+Kaiser-Squires shear plus shape noise, 30 log bins 0.5'-240', n_max = 40, Map^3 at 2', 4', 8',
+16', FP32 moments with the BF16x3 tensor-core contraction. Beside it: the plain FP64 GPU path on
+an exact centre subset of the same catalog (extrapolated by pairs), the precision form against
+the oracle on sampled centres, the 200k-galaxy lognormal catalog, the differentiation and
+batching forms, the combined estimator and the oracle on the host cores. With N GPUs (torchrun)
+every rank measures its own catalog realisation (independent problems, weak scaling, no
+data-path collective).
 
 Prints one JSON line on rank 0. ``--impl reference`` times the FP64 CPU oracle on a bounded
 centre sample of the same workload instead.
@@ -28,29 +34,41 @@ if ROOT not in sys.path:
 
 METRIC = "neighbour-pair harmonic accumulations/s; catalogs/s vs FP64 GPU path at ≤1e-4 Map³ err"
 UNIT = "pair-accumulations/s"
-PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (derived; FP32 FMA pipe)"
+# FP32 FMA pipe of a GB300: 152 SMs x 128 FP32 lanes x 2 flop per FMA x 2070 MHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
+PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (derived from unit counts and clock)"
+DEFAULT_WORKLOAD = "masked_lognormal_1m"
+MOMENT_KERNEL_NMAX = (4, 10, 20, 30, 40, 50)  # compiled order sets of moments_kernel<T, NMAX>
 
 
 def _measured_hbm_gbs():
     try:
         with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["hbm_gbs"])
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
     except (OSError, KeyError, ValueError):
-        return 6800.0  # fallback: one earlier copy measurement on a GB300
+        return 6800.0, "fallback 6.8 TB/s (one earlier copy measurement on a GB300; of fallback)"
 
 
-HBM_PEAK_GBS = _measured_hbm_gbs()
-# DRAM bytes (read + write) per launch of the current moments kernel at the lognormal_200k
-# workload: ncu capture at 50 000 galaxies (profiles/moments_kernel_lognormal_50k.md) scaled to
-# 200 000 centres (the traffic is the G/W write, proportional to the number of centres).
-# Set to None whenever the kernel changes until it is captured again.
-MOMENTS_TRAFFIC_BYTES = 4 * (125.665792e6 + 1052.680e6)
-# DRAM bytes per launch of the tensor-core contraction (BF16x3) at lognormal_200k, from an ncu
-# capture scaled by the centres, or None. None now: the kernel has since been changed to read only
-# each Z1's centre range (the same work at one z-bin); its last capture, 4 x (1.066084e9 +
-# 9.231360e6) bytes, is kept in profiles/contract_tc_bf16x3_lognormal_50k.md.
-CONTRACT_TRAFFIC_BYTES = None
+HBM_PEAK_GBS, HBM_PEAK_NOTE = _measured_hbm_gbs()
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands, per
+# (kernel, workload), scaled to the workload's centres where the capture was a smaller catalog of
+# the same density (the traffic of both kernels is proportional to the centres); None until the
+# kernel has been captured since its last change.
+TRAFFIC_BYTES = {
+    ("moments", "masked_lognormal_1m"): None,
+    ("moments", "lognormal_200k"): None,
+    ("contract", "masked_lognormal_1m"): None,
+    ("contract", "lognormal_200k"): None,
+}
+TRAFFIC_NOTE = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (profiles/)"
+
+
+def compiled_nmax(n_max: int) -> int:
+    """n_max of the moment kernel instantiation that serves n_max (the smallest compiled set)."""
+    for k in MOMENT_KERNEL_NMAX:
+        if n_max <= k:
+            return k
+    raise ValueError("n_max above the compiled range")
 
 
 def flops_per_pair(n_max: int) -> int:
@@ -141,11 +159,16 @@ def workload_setup(name: str, n: int = 0):
 
 
 def workload_config(name, p, precision):
+    """The workload a bench line measures; both arms print the same dict (the reference arm's own
+    arithmetic, FP64, is in its dtype)."""
     return {"workload": name, "n_galaxies": p["n"], "patch_arcmin": p["side"], "field": p["field"],
-            "n_bins": p["n_bins"], "theta_min_arcmin": p["theta_min"], "theta_max_arcmin": p["theta_max"],
-            "n_max": p["n_max"], "n_phi": 100, "theta_ap_arcmin": p["theta_ap"], "precision": precision,
-            "l2": "inputs (catalog 4 MB) are L2-resident by design; a 256 MiB buffer is written "
-                  "between steps to flush L2", "parallelism": "one catalog per GPU"}
+            "masked_holes": bool(p.get("holes", False)), "n_bins": p["n_bins"],
+            "theta_min_arcmin": p["theta_min"], "theta_max_arcmin": p["theta_max"], "n_max": p["n_max"],
+            "n_phi": 100, "theta_ap_arcmin": ",".join("%g" % t for t in p["theta_ap"]),
+            "precision": precision,
+            "l2": "inputs (catalog %d MB) are L2-resident by design; a 256 MiB buffer is written "
+                  "between steps to flush L2" % max(1, int(round(p["n"] * 24 / 1e6))),
+            "parallelism": "one catalog per GPU"}
 
 
 # ------------------------------------------------------------------ oracle (CPU) timing
@@ -176,34 +199,52 @@ def oracle_sample(cat, setup, theta, target_s: float, seed: int = 0):
     return pairs, sec, k, oracle.num_threads()
 
 
-def measure_adjoint(api, est, dev, theta, stream):
-    """One forward and one backward of the differentiable Map^3 (api.map3) on the bench catalog,
-    each timed with CUDA events (after one untimed pair); L = sum of the Map^3 measures."""
+def measure_adjoint(api, precision: str, stream):
+    """The differentiation form on its own workload (grad_lognormal_500k: 5e5 galaxies on 420',
+    20 bins 0.5'-120', n_max 30, Map^3 at 4', 8', 16'): one forward and one backward of the
+    differentiable Map^3 (api.map3, L = sum of Map^3 over the apertures), each timed with CUDA
+    events after one untimed pair."""
     import torch
+    from paper_2309_08601_gb300 import synth
+    p, setup, theta = workload_setup("grad_lognormal_500k")
+    cat = synth.workload_catalog("grad_lognormal_500k")
+    dev = api.catalog_to_device(cat)
     xq, yq, g1, g2, w = dev[:5]
+    with api.Estimator(**setup, precision=precision, stream=stream) as est:
+        def once():
+            a1, a2, aw = (t.clone().requires_grad_(True) for t in (g1, g2, w))
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            m8 = api.map3(est, xq, yq, a1, a2, aw, theta)
+            L = m8[..., 0].sum()
+            ev[1].record(stream)
+            L.backward()
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            return ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), (a1.grad, a2.grad, aw.grad), L
 
-    def once():
-        a1, a2, aw = (t.clone().requires_grad_(True) for t in (g1, g2, w))
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        ev[0].record(stream)
-        m8 = api.map3(est, xq, yq, a1, a2, aw, theta)
-        L = m8[..., 0].sum()
-        ev[1].record(stream)
-        L.backward()
-        ev[2].record(stream)
-        torch.cuda.synchronize()
-        return ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), a1.grad, float(L.detach())
-
-    once()
-    fwd, bwd, gr, L = once()
-    return {"loss": "sum of Map^3 over the apertures", "forward_ms": fwd, "backward_ms": bwd,
-            "backward_over_forward": bwd / fwd, "grad_finite": bool(torch.isfinite(gr).all()),
+        once()
+        fwd, bwd, grads, L = once()
+        # exact identities of the gradient: Map^3 is cubic in the shears and of degree 0 in the
+        # weights, so sum g dL/dg = 3 L and sum w dL/dw = 0
+        eg = float((g1.double() * grads[0].double() + g2.double() * grads[1].double()).sum())
+        ew = w.double() * grads[2].double()
+        Lf = float(L.detach())
+    return {"workload": "grad_lognormal_500k: %d galaxies on %g', %d bins %g'-%g', n_max %d"
+                        % (cat.n, p["side"], p["n_bins"], p["theta_min"], p["theta_max"], p["n_max"]),
+            "loss": "sum of Map^3 over the apertures", "forward_ms": fwd, "backward_ms": bwd,
+            "backward_over_forward": bwd / fwd,
+            "grad_finite": bool(all(torch.isfinite(g).all() for g in grads)),
+            "homogeneity_rel_err_gamma": abs(eg - 3 * Lf) / max(abs(3 * Lf), 1e-300),
+            "homogeneity_rel_err_w": abs(float(ew.sum())) / max(float(ew.abs().sum()), 1e-300),
             "kernels": "map3/to_gamma/edge_correct adjoints, contraction adjoint, moments adjoint"}
 
 
-def measure_batch(api, n_real: int, precision: str, stream):
+def measure_batch(api, n_real: int, precision: str, stream, fp64_frac: float):
     """n_real realisations of the tomographic batching workload through one mp3pcf_run_batch call
-    (the largest catalog sizes the workspace, the others replay a captured CUDA graph)."""
+    (the largest catalog sizes the workspace, the others replay a captured CUDA graph), and the
+    plain FP64 GPU path on an exact random centre subset of the first realisation, extrapolated to
+    the whole realisation by its pairs."""
     import torch
     from paper_2309_08601_gb300 import synth
     tp = synth.WORKLOADS["tomo_64x5_lognormal"]
@@ -214,10 +255,10 @@ def measure_batch(api, n_real: int, precision: str, stream):
     devs = [api.catalog_to_device(c) for c in cats]
     ext = (0, 0, int(np.ceil(tp["side"] / synth.QUANTUM)), int(np.ceil(tp["side"] / synth.QUANTUM)))
     with api.Estimator(**bset, precision=precision, stream=stream) as eb:
-        pairs = 0
+        pairs_each = []
         for d in devs:  # untimed: the pair counter holds the last accumulation
             eb.accumulate_moments(*d[:5], zbin=d[5])
-            pairs += eb.counts()[1]
+            pairs_each.append(eb.counts()[1])
         torch.cuda.synchronize()
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0.record(stream)
@@ -227,11 +268,48 @@ def measure_batch(api, n_real: int, precision: str, stream):
         sec = t0.elapsed_time(t1) / 1e3
         launches, inst = eb.graph_stats()
         finite = bool(torch.isfinite(m8).all())
-    return {"workload": "tomo_64x5_lognormal: %d of the 64 realisations, 5 z-bins of U{50k..400k} "
-                        "galaxies on 300', all 125 Z-triplets" % n_real,
-            "galaxies": [int(c.n) for c in cats], "pairs": int(pairs), "seconds": sec,
-            "catalogs_per_s": n_real / sec, "pairs_per_s": pairs / sec,
-            "graph_launches": launches, "graph_instantiations": inst, "m8_finite": finite}
+    pairs = int(sum(pairs_each))
+    out = {"workload": "tomo_64x5_lognormal: %d of the 64 realisations, 5 z-bins of U{50k..400k} "
+                       "galaxies on 300', all 125 Z-triplets" % n_real,
+           "galaxies": [int(c.n) for c in cats], "pairs": pairs, "seconds": sec,
+           "catalogs_per_s": n_real / sec, "pairs_per_s": pairs / sec,
+           "seconds_for_64_extrapolated": 64 * sec / n_real,
+           "extrapolation": "64 realisations at the measured seconds per realisation (counts are drawn "
+                            "from the same distribution)",
+           "graph_launches": launches, "graph_instantiations": inst, "m8_finite": finite}
+    if fp64_frac > 0:
+        c0 = cats[0]
+        rng = np.random.default_rng(13)
+        sel = torch.as_tensor((rng.random(c0.n) < fp64_frac).astype(np.uint8), device="cuda")
+        d0 = devs[0]
+        res = {}
+        for prec in ("fp64", precision):
+            with api.Estimator(**bset, precision=prec, stream=stream) as e:
+                e.measure(*d0[:5], theta_ap=bth, zbin=d0[5], centre_mask=sel, report_singular=False)
+                torch.cuda.synchronize()
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                m = e.measure(*d0[:5], theta_ap=bth, zbin=d0[5], centre_mask=sel, report_singular=False)
+                a1.record(stream)
+                torch.cuda.synchronize()
+                res[prec] = (a0.elapsed_time(a1) / 1e3, e.counts()[1], m.m8.cpu().numpy())
+        s64, p64, m64 = res["fp64"]
+        sp, _, mp = res[precision]
+        frac = p64 / pairs_each[0]
+        fp64_cat_s = frac / s64  # realisations per second, extrapolated by pairs
+        auto = np.zeros(m64.shape[0], bool)
+        for z in range(tp["n_z"]):
+            auto[(z * tp["n_z"] + z) * tp["n_z"] + z] = True
+        out["fp64_path"] = {
+            "sample": "exact random centre subset (%.1f %% of the pairs) of realisation 0, whole path "
+                      "with those centres; catalogs/s extrapolated to the whole realisation by pairs"
+                      % (100 * frac),
+            "fp64_catalogs_per_s": fp64_cat_s, "fp64_pairs_per_s": p64 / s64,
+            "precision_over_fp64_same_subset": s64 / sp,
+            "batched_over_fp64_catalogs_per_s": (n_real / sec) / fp64_cat_s,
+            "map3_rel_err_vs_fp64_auto_triplets": float(np.abs(mp[auto, :, 0] - m64[auto, :, 0]).max() /
+                                                        np.abs(m64[auto, :, 0]).max())}
+    return out
 
 
 def measure_combined(api, precision: str, stream):
@@ -329,7 +407,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args.workload, p, "fp64-oracle"),
+            "data": "synthetic (seeded lognormal Kaiser-Squires shear + shape noise)",
+            "config": workload_config(args.workload, p, args.precision), "oracle_precision": "fp64",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": "%d random centres per step (all %d galaxies as neighbours), "
                                        "whole path" % (cents // max(args.steps, 1), cat.n)},
@@ -366,6 +445,153 @@ def whole_job(units_per_step_all_ranks: float, steps: int, seconds_max: float) -
 
 # ------------------------------------------------------------------ GPU arm
 
+def measure_peaks(native):
+    """FP32 FMA (scalar and packed two-lane) and FP64 FMA throughput of this GPU, measured by the
+    library's probe (mp3pcf_measure_peak), in TFLOP/s, with the probe's SM clock estimate."""
+    import ctypes as C
+    out = {}
+    for kind, name in ((0, "fp32_fma"), (1, "fp32_ffma2"), (2, "fp64_fma")):
+        f, mhz = C.c_double(0.0), C.c_double(0.0)
+        native.check(native.lib().mp3pcf_measure_peak(kind, None, C.byref(f), C.byref(mhz)), "measure_peak")
+        out[name + "_tflops"] = f.value / 1e12
+        out[name + "_sm_mhz_estimate"] = mhz.value
+    return out
+
+
+def time_steps(step, steps, stream):
+    """CUDA-event time (ms) of `steps` calls of step() on `stream`, L2 flushed before each."""
+    import torch
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    m = None
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        m = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), m
+
+
+def moment_roofline(name, n_max, pairs, k1_ms, precision, peaks):
+    """Roofline of stage (a) on the FP32 FMA pipe: algorithmic flops (the plain form of
+    Eq. Gn_disc, flops_per_pair) x pairs per launch / launch time, against the derived peak;
+    the kernel's own flop count and the measured probe peaks are reported beside it."""
+    fpp = flops_per_pair(n_max)
+    achieved = fpp * pairs / (k1_ms / 1e3) / 1e12
+    kfl = kernel_flops_per_pair(n_max) * pairs / (k1_ms / 1e3) / 1e12
+    r = {"bound": "alu", "kernel": "moments_kernel<float,%d>" % compiled_nmax(n_max), "achieved": achieved,
+         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+         "traffic": TRAFFIC_BYTES.get(("moments", name)) if precision != "fp64" else None,
+         "traffic_note": TRAFFIC_NOTE, "flops_per_pair": fpp, "pairs_per_launch": pairs,
+         "kernel_flops_per_pair": kernel_flops_per_pair(n_max),
+         "frac_kernel_flops": kfl / FP32_PEAK_TFLOPS, "launch_ms": k1_ms, "peak_source": PEAK_NOTE}
+    if peaks:
+        meas = max(peaks["fp32_fma_tflops"], peaks["fp32_ffma2_tflops"])
+        r["peak_measured"] = meas
+        r["frac_of_measured"] = achieved / meas
+        r["peak_measured_source"] = "mp3pcf_measure_peak: best of FP32 FMA and packed FFMA2 probes"
+    return r
+
+
+def contract_roofline(name, n_centres, n_bins, n_max, n_z, k2_ms, precision):
+    """Roofline of stage (b) on HBM: every moment row read once (complex, moment precision)."""
+    esz = 16 if precision == "fp64" else 8
+    k2_bytes = n_centres * n_z * n_bins * ((2 * n_max + 3) + (2 * n_max + 1)) * esz
+    achieved = k2_bytes / (k2_ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": "contract (%s)" % precision, "achieved": achieved, "peak": HBM_PEAK_GBS,
+            "unit": "GB/s", "frac": achieved / HBM_PEAK_GBS, "bytes_per_launch": k2_bytes, "launch_ms": k2_ms,
+            "peak_source": HBM_PEAK_NOTE,
+            "traffic": TRAFFIC_BYTES.get(("contract", name)) if precision == "bf16x3" else None,
+            "traffic_note": TRAFFIC_NOTE}
+
+
+def measure_fp64_subset(api, dev, n, setup, theta, pairs_full, precision, stream, frac, seed=11):
+    """The plain FP64 GPU path (FP64 moments, FP64 CUDA-core contraction, FP64 post-processing)
+    on an exact random centre subset of the catalog, and the precision form on the same centres;
+    FP64 catalogs/s extrapolated to the whole catalog by its pairs."""
+    import torch
+    rng = np.random.default_rng(seed)
+    sel = torch.as_tensor((rng.random(n) < frac).astype(np.uint8), device="cuda")
+    res = {}
+    for prec in ("fp64", precision):
+        with api.Estimator(**setup, precision=prec, stream=stream) as e:
+            e.measure(*dev[:5], theta_ap=theta, centre_mask=sel, report_singular=False)
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            m = e.measure(*dev[:5], theta_ap=theta, centre_mask=sel, report_singular=False)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            res[prec] = (a0.elapsed_time(a1) / 1e3, e.counts(), m.m8.cpu().numpy())
+    s64, (nc, p64), m64 = res["fp64"]
+    sp, _, mp = res[precision]
+    share = p64 / pairs_full
+    return {"sample": "exact random centre subset: %d centres (%.2f %% of the pairs), whole path with "
+                      "those centres; catalogs/s extrapolated to the whole catalog by pairs" % (nc, 100 * share),
+            "catalogs_per_s": share / s64, "pairs_per_s": p64 / s64, "seconds_subset": s64,
+            "precision_over_fp64_same_subset": s64 / sp,
+            "map3_rel_err_vs_fp64": float(np.abs(mp[..., 0] - m64[..., 0]).max() / np.abs(m64[..., 0]).max()),
+            "m8_rel_err_vs_fp64": float(np.abs(mp - m64).max() / np.abs(m64).max())}
+
+
+def oracle_parity(api, dev, cat, setup, theta, precision, stream, n_centres, seed=12):
+    """The precision form against the FP64 oracle on a random sample of centres (all galaxies as
+    neighbours): normwise relative errors of Upsilon, N and the eight aperture measures."""
+    import torch
+    import oracle
+    rng = np.random.default_rng(seed)
+    cen = np.sort(rng.choice(cat.n, n_centres, replace=False))
+    t0 = time.perf_counter()
+    r = oracle.pipeline(oracle.Setup(**setup), cat, theta, cen)
+    t_orc = time.perf_counter() - t0
+    mask = np.zeros(cat.n, np.uint8)
+    mask[cen] = 1
+    with api.Estimator(**setup, precision=precision, stream=stream) as e:
+        m = e.measure(*dev[:5], theta_ap=theta, centre_mask=torch.as_tensor(mask, device="cuda"),
+                      report_singular=False)
+        torch.cuda.synchronize()
+        g = {"ups": m.upsilon.cpu().numpy(), "norm": m.norm.cpu().numpy(), "m8": m.m8.cpu().numpy()}
+
+    def rel(a, b):
+        ok = np.isfinite(b)
+        return float(np.abs(a[ok] - b[ok]).max() / np.abs(b[ok]).max())
+
+    return {"centres": int(n_centres), "oracle_seconds": t_orc, "upsilon_rel_err": rel(g["ups"], r.ups),
+            "norm_rel_err": rel(g["norm"], r.norm), "m8_rel_err": rel(g["m8"], r.m8),
+            "map3_rel_err": rel(g["m8"][..., 0], r.m8[..., 0])}
+
+
+def measure_workload(api, name, precision, stream, steps, warmup, seed_offset=0):
+    """A few timed steps of the whole path on another workload (same method as the headline)."""
+    import torch
+    from paper_2309_08601_gb300 import synth
+    p, setup, theta = workload_setup(name)
+    cat = synth.make_catalog(p["n"], p["side"], p["seed"] + seed_offset, field=p["field"], weights=p["weights"],
+                             holes=p.get("holes", False))
+    dev = api.catalog_to_device(cat)
+    with api.Estimator(**setup, precision=precision, stream=stream) as est:
+        def step():
+            return est.measure(*dev[:5], theta_ap=theta, report_singular=False)
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        n_centres, pairs = est.counts()
+        est.set_timing(True)
+        est.stage_times(reset=True)
+        ms, _ = time_steps(step, steps, stream)
+        stages = est.stage_times(reset=True)
+        est.set_timing(False)
+    k1 = stages["moments"][0] / steps
+    k2 = stages["contract"][0] / steps
+    return {"workload": name, "n_galaxies": p["n"], "ms_per_step": ms / steps, "catalogs_per_s": 1e3 * steps / ms,
+            "pairs_per_catalog": pairs, "pairs_per_s": pairs * steps / (ms / 1e3),
+            "stage_ms_per_step": {k: v[0] / steps for k, v in stages.items()},
+            "roofline": moment_roofline(name, p["n_max"], pairs, k1, precision, None),
+            "roofline_contract": contract_roofline(name, n_centres, p["n_bins"], p["n_max"], 1, k2, precision)}
+
+
 def run_gpu(args):
     import torch
 
@@ -386,6 +612,7 @@ def run_gpu(args):
     if dist is not None:
         dist.barrier()
     native.lib()
+    peaks = measure_peaks(native) if (rank == 0 and args.peaks) else None
 
     p, setup, theta = workload_setup(args.workload, args.n)
     cat = synth.make_catalog(p["n"], p["side"], rank_seed(p["seed"], rank), field=p["field"],
@@ -393,7 +620,6 @@ def run_gpu(args):
     dev = api.catalog_to_device(cat)
     stream = torch.cuda.current_stream()
     est = api.Estimator(**setup, precision=args.precision, stream=stream)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def step():
         return est.measure(*dev[:5], theta_ap=theta, report_singular=False)
@@ -410,18 +636,10 @@ def run_gpu(args):
     time.sleep(0.3)
     if dist is not None:
         dist.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        m = step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    ms, m = time_steps(step, args.steps, stream)
     if dist is not None:
         dist.barrier()
     clocks.stop()
-    ms = ev0.elapsed_time(ev1)
     stages = est.stage_times(reset=True)
     est.set_timing(False)
     ms_max = reduce_over_ranks([ms], "max", dist)[0]
@@ -429,48 +647,25 @@ def run_gpu(args):
     sec = ms_max / 1e3
     value = whole_job(pairs_all, args.steps, sec)
     cat_per_s = whole_job(world, args.steps, sec)
-
-    # ---- roofline of the dominant kernel (stage a, FP32 FMA pipe)
     k1_ms = stages["moments"][0] / args.steps
-    fpp = flops_per_pair(p["n_max"])
-    achieved = fpp * pairs / (k1_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": "moments_kernel<float,30>", "achieved": achieved,
-                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                "traffic": (args.k1_traffic if args.k1_traffic is not None else
-                            (MOMENTS_TRAFFIC_BYTES if (args.workload == "lognormal_200k" and not args.n
-                                                       and args.precision != "fp64") else None)),
-                "traffic_note": "ncu DRAM read+write, capture at 50 000 galaxies scaled by centres",
-                "flops_per_pair": fpp, "pairs_per_launch": pairs,
-                "kernel_flops_per_pair": kernel_flops_per_pair(p["n_max"]),
-                "frac_kernel_flops": kernel_flops_per_pair(p["n_max"]) * pairs / (k1_ms / 1e3) / 1e12
-                / FP32_PEAK_TFLOPS,
-                "launch_ms": k1_ms, "peak_source": PEAK_NOTE}
-    launches = sum(v[1] for v in stages.values())
-    # ---- stage (b): HBM-bound; algorithmic bytes = every moment row read once (complex, moment
-    # precision) + the FP64 partial sums written and read once by the slice reduction
     k2_ms = stages["contract"][0] / args.steps
-    esz = 16 if args.precision == "fp64" else 8
-    nbins, nmax = p["n_bins"], p["n_max"]
-    k2_bytes = n_centres * nbins * ((2 * nmax + 3) + (2 * nmax + 1)) * esz
-    roofline_contract = {"bound": "hbm", "kernel": "contract (%s)" % args.precision,
-                         "achieved": k2_bytes / (k2_ms / 1e3) / 1e9, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                         "frac": k2_bytes / (k2_ms / 1e3) / 1e9 / HBM_PEAK_GBS, "bytes_per_launch": k2_bytes,
-                         "launch_ms": k2_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                         "traffic": (CONTRACT_TRAFFIC_BYTES if (args.workload == "lognormal_200k" and not args.n
-                                                                and args.precision == "bf16x3") else None),
-                         "traffic_note": "ncu DRAM read+write, capture at 50 000 galaxies scaled by centres"}
+    roofline = moment_roofline(args.workload if not args.n else "", p["n_max"], pairs, k1_ms, args.precision, peaks)
+    roofline_contract = contract_roofline(args.workload if not args.n else "", n_centres, p["n_bins"], p["n_max"],
+                                          1, k2_ms, args.precision)
+    launches = sum(v[1] for v in stages.values())
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers (pinned), copies inside the region
     host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
             (cat.xq, cat.yq, cat.g1, cat.g2, cat.w)]
     h2d = sum(h.numel() * h.element_size() for h in host)
     out_host = torch.empty((1, len(theta), 8), dtype=torch.float64).pin_memory()
     d2h = out_host.numel() * out_host.element_size()
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for k in range(args.steps):
+    for k in range(e2e_steps):
         for d, h in zip(dev[:5], host):
             d.copy_(h, non_blocking=True)
         m = step()
@@ -478,10 +673,9 @@ def run_gpu(args):
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_s = reduce_over_ranks([e2e_s], "max", dist)[0]
-    e2e = {"value": whole_job(pairs_all, args.steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h}
+    e2e = {"value": whole_job(pairs_all, e2e_steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "steps": e2e_steps}
 
-    m8_fp32 = m.m8.cpu().numpy()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64",
@@ -489,39 +683,36 @@ def run_gpu(args):
             "config": workload_config(args.workload, p, args.precision),
             "catalogs_per_s": cat_per_s, "pairs_per_catalog": pairs,
             "pairs_per_s_moments_kernel": pairs / (k1_ms / 1e3),
-            "moment_terms_per_s": pairs * ((2 * nmax + 3) + (2 * nmax + 1)) / (k1_ms / 1e3),
+            "moment_terms_per_s": pairs * ((2 * p["n_max"] + 3) + (2 * p["n_max"] + 1)) / (k1_ms / 1e3),
             "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
             "roofline": roofline, "roofline_contract": roofline_contract, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks.summary()}
+    if peaks:
+        line["peaks_measured"] = peaks
+    est.close()
 
-    # ---- the plain FP64 GPU path on the same catalog (rank 0, one untimed-warmup + one run)
-    if rank == 0 and args.fp64_compare:
-        with api.Estimator(**setup, precision="fp64", stream=stream) as e64:
-            sub = torch.zeros(cat.n, dtype=torch.uint8, device="cuda")
-            sub[:64] = 1
-            e64.measure(*dev[:5], theta_ap=theta, centre_mask=sub, report_singular=False)
-            torch.cuda.synchronize()
-            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a0.record(stream)
-            m64 = e64.measure(*dev[:5], theta_ap=theta, report_singular=False)
-            a1.record(stream)
-            torch.cuda.synchronize()
-            s64 = a0.elapsed_time(a1) / 1e3
-            m8_64 = m64.m8.cpu().numpy()
-        err = float(np.abs(m8_fp32[..., 0] - m8_64[..., 0]).max() / np.abs(m8_64[..., 0]).max())
-        err_all = float(np.abs(m8_fp32 - m8_64).max() / np.abs(m8_64).max())
-        line["fp64_path"] = {"catalogs_per_s": 1.0 / s64, "pairs_per_s": pairs / s64,
-                             "speedup_of_measured_path": (cat_per_s / world) * s64,
-                             "map3_rel_err_vs_fp64": err, "m8_rel_err_vs_fp64": err_all}
+    # ---- the plain FP64 GPU path on an exact centre subset of the same catalog (rank 0)
+    if rank == 0 and args.fp64_frac > 0:
+        line["fp64_path"] = measure_fp64_subset(api, dev, cat.n, setup, theta, pairs, args.precision, stream,
+                                                args.fp64_frac)
+        line["fp64_path"]["speedup_of_measured_path"] = (cat_per_s / world) / line["fp64_path"]["catalogs_per_s"]
 
-    # ---- the differentiation form on the same catalog: forward + backward through api.map3
+    # ---- the precision form against the oracle on sampled centres (rank 0)
+    if rank == 0 and args.oracle_centres > 0:
+        line["oracle_parity"] = oracle_parity(api, dev, cat, setup, theta, args.precision, stream,
+                                              args.oracle_centres)
+
+    # ---- the 200k-galaxy lognormal workload, a few steps (rank 0)
+    if rank == 0 and args.extra_workload and args.extra_workload != args.workload:
+        line["extra_workload"] = measure_workload(api, args.extra_workload, args.precision, stream, 3, 1)
+
+    # ---- the differentiation form on its own workload (rank 0)
     if rank == 0 and args.adjoint:
-        line["adjoint"] = measure_adjoint(api, est, dev, theta, stream)
+        line["adjoint"] = measure_adjoint(api, args.precision, stream)
 
-    # ---- the batching form: whole tomographic realisations (5 z-bins of 50k-400k galaxies)
-    # through mp3pcf_run_batch with CUDA graphs, rank 0; pairs counted by an untimed pass
+    # ---- the batching form: whole tomographic realisations through mp3pcf_run_batch (rank 0)
     if rank == 0 and args.batch_realisations > 0:
-        line["batch"] = measure_batch(api, args.batch_realisations, args.precision, stream)
+        line["batch"] = measure_batch(api, args.batch_realisations, args.precision, stream, args.fp64_frac)
 
     # ---- the combined estimator against the discrete one (rank 0)
     if rank == 0 and args.combined:
@@ -529,10 +720,10 @@ def run_gpu(args):
 
     if rank == 0 and args.cpu_baseline:
         import oracle
-        pr, sec, k, threads = oracle_sample(cat, setup, theta, target_s=args.cpu_s)
-        line["cpu_baseline"] = {"value": pr / sec, "unit": UNIT, "cores": threads, "kind": "oracle",
+        pr, sec_o, k, threads = oracle_sample(cat, setup, theta, target_s=args.cpu_s)
+        line["cpu_baseline"] = {"value": pr / sec_o, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": "%d random centres (all %d galaxies as neighbours), whole "
-                                          "path, %.1f s" % (k, cat.n, sec),
+                                          "path, %.1f s" % (k, cat.n, sec_o),
                                 "cpu_model": cpu_model()}
         if threads > 1:
             oracle.set_num_threads(1)
@@ -543,7 +734,6 @@ def run_gpu(args):
                 "sample": "%d random centres, whole path, %.1f s" % (k1, sec1)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    est.close()
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -556,25 +746,29 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="lognormal_200k")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--n", type=int, default=0,
                     help="rescale the workload to n galaxies at the same density (profiling runs)")
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp32", "fp64"],
                     help="bf16x3 (default): FP32 moments, BF16 hi+lo tensor-core contraction, FP64 "
                          "edge correction and sums")
-    ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end (host buffer) timing")
+    ap.add_argument("--fp64-frac", type=float, default=0.005,
+                    help="fraction of centres for the FP64 GPU path subset (0: skip)")
+    ap.add_argument("--oracle-centres", type=int, default=48,
+                    help="centres of the precision form checked against the oracle (0: skip)")
+    ap.add_argument("--extra-workload", default="lognormal_200k",
+                    help="a second workload timed for a few steps ('' to skip)")
+    ap.add_argument("--no-peaks", dest="peaks", action="store_false", help="skip the FP32/FP64 pipe probes")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work sampled")
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false",
                     help="skip the forward + backward timing of the differentiable Map^3")
-    ap.add_argument("--batch-realisations", type=int, default=2,
+    ap.add_argument("--batch-realisations", type=int, default=8,
                     help="tomographic realisations timed through mp3pcf_run_batch (0: skip)")
     ap.add_argument("--no-combined", dest="combined", action="store_false",
                     help="skip the combined-versus-discrete estimator timing")
     ap.add_argument("--ref-step-s", type=float, default=8.0)
-    ap.add_argument("--k1-traffic", type=float, default=None,
-                    help="DRAM bytes per moments launch (default: the committed ncu figure, at "
-                         "the lognormal_200k workload only)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
