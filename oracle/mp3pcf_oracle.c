@@ -495,9 +495,11 @@ int orc_cen_factor(int mu, double t1, double t2, double phi, double* out)
     return ORC_OK;
 }
 
+/* projection 0: x-projection at phi_k; 1: centroid projection at phi_k; 2: x-projection averaged
+ * over the angular bin around phi_k (Sec. 2.4, the binned 3PCF) */
 int orc_to_gamma(const orc_cfg* c, const double* gam_in, int32_t projection, double* out)
 {
-    if (!cfg_ok(c)) return ORC_EINVAL;
+    if (!cfg_ok(c) || projection < 0 || projection > 2) return ORC_EINVAL;
     const int nb = c->n_bins, nmax = c->n_max, D = 2 * nmax + 1, np = c->n_phi;
     double* e = (double*)malloc(sizeof(double) * (nb + 1));
     orc_edges(c, e, NULL);
@@ -514,7 +516,10 @@ int orc_to_gamma(const orc_cfg* c, const double* gam_in, int32_t projection, dou
             cplx s = 0;
             for (int nn = -nmax; nn <= nmax; ++nn) {
                 const cplx gn = gam[((size_t)zm * D + (nn + nmax)) * nb * nb + (size_t)b1 * nb + b2];
-                s += gn * (cos(nn * phi) + I * sin(nn * phi));
+                /* projection 2: mean of e^{i n phi} over [phi - h, phi + h), h = pi / np */
+                const double h = M_PI / np;
+                const double avg = (projection == 2 && nn != 0) ? sin(nn * h) / (nn * h) : 1.0;
+                s += gn * avg * (cos(nn * phi) + I * sin(nn * phi));
             }
             if (projection == 1) s *= cen_factor(mu, radial_node(c, e, b1), radial_node(c, e, b2), phi);
             gp[(((size_t)zm * nb + b1) * nb + b2) * np + k] = s;
@@ -679,6 +684,59 @@ int orc_to_map3(const orc_cfg* c, const double* gcen_in, int64_t n_ap, const dou
     }
     free(e);
     return ORC_OK;
+}
+
+/* ---- the shorter four-equation form of the aperture measures (App. C, Eqs. MapTrafo4_1-4):
+ *        Map^3          = Re[A123 + A132 + A231 + M3] / 4
+ *        <Map^2 Mx>     = Im[-A123 + A132 + A231 + M3] / 4
+ *        <Map Mx^2>     = Re[A123 + A132 - A231 - M3] / 4
+ *        <Mx^3>         = Im[A123 + A132 + A231 - M3] / 4
+ *      with M3 = <M^3>(t1, t2, t3) and Aabc the correlator with one conjugated factor at the radii
+ *      (ta, tb, tc). As printed, the equations place the conjugate on the LAST radius of each list
+ *      (<M^2 M^*>, the convention of the paper's reference for these forms): with the conjugate
+ *      first, as <M^* M^2> is defined in Eq. MFrom3pcfTheory, A123 and A132 would be the same
+ *      number and no term would conjugate t3, and the four measures would not be recovered. So
+ *      Aabc = <M^* M^2>(tc, ta, tb): the Gamma_1 / F_1 correlator at (t3, t1, t2), (t2, t1, t3) and
+ *      (t1, t2, t3). It equals the eight-equation form where the correlators obey the relabelling
+ *      symmetries the appendix invokes, i.e. up to the quadrature and binning of the estimated
+ *      3PCF. ---- */
+int orc_combine4(const double* m3, const double* a123, const double* a132, const double* a231, double* m4)
+{
+    const cplx M3 = m3[0] + I * m3[1];
+    const cplx A123 = a123[0] + I * a123[1], A132 = a132[0] + I * a132[1], A231 = a231[0] + I * a231[1];
+    m4[0] = creal(A123 + A132 + A231 + M3) / 4.0;
+    m4[1] = cimag(-A123 + A132 + A231 + M3) / 4.0;
+    m4[2] = creal(A123 + A132 - A231 - M3) / 4.0;
+    m4[3] = cimag(A123 + A132 + A231 - M3) / 4.0;
+    return ORC_OK;
+}
+
+/* m4 [n_z^3][n_ap][4] = (Map^3, <Map^2 Mx>, <Map Mx^2>, <Mx^3>) at each radii triple */
+int orc_to_map3_four(const orc_cfg* c, const double* gcen_in, int64_t n_ap, const double* theta_ap,
+                     double* m4_out)
+{
+    if (!cfg_ok(c) || n_ap < 0) return ORC_EINVAL;
+    const int64_t z3 = nz3(c), na = n_ap > 0 ? n_ap : 1;
+    double* th3 = (double*)malloc(sizeof(double) * 9 * na);
+    double* corr = (double*)malloc(sizeof(double) * 2 * 4 * z3 * 3 * na);
+    double* m8 = (double*)malloc(sizeof(double) * 8 * z3 * 3 * na);
+    for (int64_t a = 0; a < n_ap; ++a) {
+        const double t1 = theta_ap[3 * a], t2 = theta_ap[3 * a + 1], t3 = theta_ap[3 * a + 2];
+        const double order[3][3] = {{t3, t1, t2}, {t2, t1, t3}, {t1, t2, t3}};  /* A123, A132, A231 */
+        for (int q = 0; q < 3; ++q)
+            for (int i = 0; i < 3; ++i) th3[(3 * a + q) * 3 + i] = order[q][i];
+    }
+    int st = orc_to_map3(c, gcen_in, 3 * n_ap, th3, corr, m8);
+    if (st == ORC_OK)
+        for (int64_t zt = 0; zt < z3; ++zt)
+            for (int64_t a = 0; a < n_ap; ++a) {
+                const double* cc = corr + 2 * (zt * 3 * n_ap + 3 * a) * 4;  /* [ordering][mu] complex */
+                orc_combine4(cc + 16, cc + 2, cc + 8 + 2, cc + 16 + 2, m4_out + (zt * n_ap + a) * 4);
+            }
+    free(th3);
+    free(corr);
+    free(m8);
+    return st;
 }
 
 /* ---- brute-force triplet sums straight from the definitions (Sec. 2.2 Eqs. Gamma0_def -

@@ -77,6 +77,8 @@ def lib():
             "orc_filter": [C.c_int32, C.c_double, C.c_double, C.c_double, P, P],
             "orc_cen_factor": [C.c_int32, C.c_double, C.c_double, C.c_double, P],
             "orc_combine8": [P, P],
+            "orc_to_map3_four": [P, P, I64, P, P],
+            "orc_combine4": [P, P, P, P, P],
             "orc_brute": [P, I64, P, P, P, P, P, P, C.c_int32, P, P, P, P, P, P],
             "orc_num_threads": [],
             "orc_map3_direct_brute": [I64, P, P, P, P, P, C.c_double, C.c_double, C.c_double, P, C.c_double,
@@ -313,6 +315,27 @@ def to_map3(s: Setup, gamma_cen, theta_ap):
     return corr, m8
 
 
+def to_map3_four(s: Setup, gamma_cen, theta_ap):
+    """The four-equation form (App. C): m4 [n_z^3][n_ap][4] = (Map^3, <Map^2 Mx>, <Map Mx^2>,
+    <Mx^3>) from <M^3> and the Gamma_1 correlator at three orderings of the radii."""
+    th = _c(np.atleast_2d(theta_ap), np.float64)
+    n_ap = th.shape[0]
+    m4 = np.zeros((s.n_z ** 3, n_ap, 4))
+    gc = _c(gamma_cen, np.complex128)
+    cfg = s.c()
+    _check(lib().orc_to_map3_four(C.byref(cfg), _p(gc), n_ap, _p(th), _p(m4)))
+    return m4
+
+
+def combine4(m3, a123, a132, a231) -> np.ndarray:
+    """Eqs. MapTrafo4_1-4 from <M^3>(t1, t2, t3) and the one-conjugate correlators A123, A132,
+    A231 (conjugate on the last radius of each ordering), each a complex number."""
+    vals = [_c(np.array([complex(v)]), np.complex128) for v in (m3, a123, a132, a231)]
+    out = np.zeros(4)
+    _check(lib().orc_combine4(*[_p(v) for v in vals], _p(out)))
+    return out
+
+
 def filter_F(mu: int, t1: float, t2: float, phi: float, theta) -> complex:
     th = _c(theta, np.float64)
     out = np.zeros(2)
@@ -388,6 +411,6 @@ def pipeline(s: Setup, cat, theta_ap, centres: Optional[np.ndarray] = None) -> R
 
 
 __all__ = ["Setup", "build_oracle", "edges", "moments", "count_pairs", "contract",
-           "edge_correct", "degenerate_correction", "to_gamma", "to_map3", "filter_F", "cen_factor", "combine8", "brute",
+           "edge_correct", "degenerate_correction", "to_gamma", "to_map3", "to_map3_four", "combine4", "filter_F", "cen_factor", "combine8", "brute",
            "pipeline", "num_threads", "set_num_threads", "map3_direct", "grid_catalog", "combined_moments", "Result",
            "Brute"]

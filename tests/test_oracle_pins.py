@@ -316,7 +316,9 @@ def test_to_gamma_converges_to_binned_triplet_sums(orc):
     projection the brute force applies each triplet's own factor at its exact radii, to_gamma
     the factor at the radial nodes, so narrow radial bins are used and only b1 != b2 blocks are
     compared (for b1 = b2 the exact factor of a nearly isosceles triplet flips sign near
-    phi = pi). A flipped exponent (Gamma(-phi) returned for Gamma(phi)) does not converge."""
+    phi = pi). Projection 2, the bin average in closed form (Sec. 2.4, the binned 3PCF), on the
+    brute force's own bins converges the same way and matches the sampled averages. A flipped
+    exponent (Gamma(-phi) returned for Gamma(phi)) does not converge."""
     rng = np.random.default_rng(7)
     n = 400
     xy = rng.uniform(0, 10, (n, 2))
@@ -330,7 +332,7 @@ def test_to_gamma_converges_to_binned_triplet_sums(orc):
     def bin_avg(out):
         return out.reshape(out.shape[:-1] + (K, S)).mean(-1) / K
 
-    ex, ec, eflip = [], [], []
+    ex, ec, eflip, eb = [], [], [], []
     for nmax in (10, 40, 160, 640):
         s = orc.Setup(**setup, n_max=nmax)
         G, W = orc.moments(s, cat)
@@ -345,6 +347,11 @@ def test_to_gamma_converges_to_binned_triplet_sums(orc):
         ex.append(rel_err(_merge0(bin_avg(out0)), _merge0(ref.ups_b)))
         eflip.append(rel_err(_merge0(bin_avg(out0[..., ::-1])), _merge0(ref.ups_b)))
         ec.append(rel_err(bin_avg(out1)[:, :, off], ref.upsc_b[:, :, off]))
+        # projection 2 (the bin average in closed form) on the brute force's own K bins
+        out2 = orc.to_gamma(orc.Setup(**setup, n_max=nmax, n_phi=K), ext, 2) / K
+        eb.append(rel_err(_merge0(out2), _merge0(ref.ups_b)))
+        assert rel_err(out2, bin_avg(out0)) < 2e-3  # 512 point samples per bin vs the closed form
+    assert all(a > b for a, b in zip(eb, eb[1:])), eb
     assert all(a > b for a, b in zip(ex, ex[1:])), ex
     assert all(a > b for a, b in zip(ec, ec[1:])), ec
     assert ex[-1] < 0.25 * ex[0] and ec[-1] < 0.35 * ec[0], (ex, ec)
@@ -414,6 +421,52 @@ def test_eight_measure_combination_inverts_the_products(orc):
             np.mean(P[0] * P[1] * X[2]), np.mean(P[0] * X[1] * X[2]), np.mean(X[0] * P[1] * X[2]),
             np.mean(X[0] * X[1] * P[2]), np.mean(X[0] * X[1] * X[2])]
     np.testing.assert_allclose(orc.combine8(c), want, rtol=1e-12, atol=1e-14)
+
+
+def test_four_measure_combination_recovers_the_products(orc):
+    """Eqs. MapTrafo4_1-4, with the conjugate of each one-conjugate correlator on the last radius of
+    its ordering: from <M^3>(t1,t2,t3) and A123 = <M1 M2 M3^*>, A132 = <M1 M3 M2^*>,
+    A231 = <M2 M3 M1^*> they return Map^3, <Map^2 Mx>, <Map Mx^2>, <Mx^3> at (t1,t2,t3) exactly,
+    whatever the joint distribution of the fields (sample moments of one set of fields obey the
+    relabelling symmetries as identities). With the conjugate on the first radius the printed
+    orderings (t1,t2,t3) and (t1,t3,t2) coincide and no term conjugates t3, which fails here."""
+    rng = np.random.default_rng(12)
+    P = rng.normal(size=(3, 40000))
+    X = rng.normal(size=(3, 40000)) * 0.6 + 0.4 * P[[1, 2, 0]]
+    P = P + 0.3 * P[[2, 0, 1]] ** 2  # skewed, correlated, distinct per radius
+    M = P + 1j * X
+
+    def last_conj(a, b, c):
+        return np.mean(M[a] * M[b] * np.conj(M[c]))
+
+    m3 = np.mean(M[0] * M[1] * M[2])
+    got = orc.combine4(m3, last_conj(0, 1, 2), last_conj(0, 2, 1), last_conj(1, 2, 0))
+    want = [np.mean(P[0] * P[1] * P[2]), np.mean(P[0] * P[1] * X[2]), np.mean(P[0] * X[1] * X[2]),
+            np.mean(X[0] * X[1] * X[2])]
+    np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-13)
+
+    def first_conj(a, b, c):
+        return np.mean(np.conj(M[a]) * M[b] * M[c])
+
+    wrong = orc.combine4(m3, first_conj(0, 1, 2), first_conj(0, 2, 1), first_conj(1, 2, 0))
+    assert np.abs(wrong - want).max() > 1e-3
+
+
+@pytest.mark.slow
+def test_four_and_eight_equation_forms_agree_within_quadrature(orc):
+    """App. C: on a noise-free lognormal field the four-equation Map^3 (built from Gamma_0 and
+    Gamma_1 alone) and the eight-equation one (all four Gamma_mu) agree to the accuracy of the
+    estimated 3PCF's binning, truncation to [theta_min, theta_max] and quadrature (a few per cent
+    at these coarse bins), and both give small parity-odd <Mx^3>."""
+    cat = make_catalog(12000, 80.0, 3, field="lognormal", sigma_e=0.0, weights="unit", ngrid=1024)
+    s = orc.Setup(n_bins=20, theta_min=0.25, theta_max=25.0, n_max=16)
+    th = [[3.0, 3.0, 3.0], [2.0, 3.0, 4.0]]
+    r = orc.pipeline(s, cat, th)
+    m4 = orc.to_map3_four(s, r.gamma_cen, th)[0]
+    m8 = r.m8[0]
+    assert np.all(m8[:, 0] > 0) and np.all(m4[:, 0] > 0)
+    np.testing.assert_allclose(m4[:, 0], m8[:, 0], rtol=0.05)
+    assert np.all(np.abs(m4[:, 3]) < 0.05 * m4[:, 0]) and np.all(np.abs(m8[:, 7]) < 0.05 * m8[:, 0])
 
 
 # --------------------------------------------- P7: physics check on a parity-even lognormal field
