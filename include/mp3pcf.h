@@ -150,7 +150,10 @@ mp3pcf_status mp3pcf_edge_correct(mp3pcf_ctx* ctx, const double* d_upsilon, cons
 /* Gamma^x_mu(b1, b2, phi_k) = sum_n Gamma_{mu,n} e^{i n phi_k}, phi_k = (k+1/2) 2 pi / n_phi
  * (Sec. 4: linear angular bins on [0, 2 pi]); projection 1 multiplies by the rotation factors
  * of Eqs. X2Centroid0-3 (Sec. 2.3) evaluated at the radial nodes of b1 and b2, giving the
- * centroid projection. Output d_gamma_phi [n_z^3][4][n_bins][n_bins][n_phi] complex double. */
+ * centroid projection; projection 2 is the x-projection averaged over each angular bin
+ * [phi_k - pi/n_phi, phi_k + pi/n_phi) (each term times sinc(n pi / n_phi)), the binned
+ * estimate of Sec. 2.4 (Eq. Gamma0_binned) that angular-bin sums of triplets compare with.
+ * Output d_gamma_phi [n_z^3][4][n_bins][n_bins][n_phi] complex double. */
 mp3pcf_status mp3pcf_to_gamma(mp3pcf_ctx* ctx, const double* d_gamma_n, int32_t projection,
                               double* d_gamma_phi);
 
@@ -166,6 +169,17 @@ mp3pcf_status mp3pcf_to_gamma(mp3pcf_ctx* ctx, const double* d_gamma_n, int32_t 
  * (EINVAL when n_ap > 0). */
 mp3pcf_status mp3pcf_to_map3(mp3pcf_ctx* ctx, const double* d_gamma_cen, int64_t n_ap,
                              const double* d_theta_ap, double* d_corr, double* d_m8);
+
+/* The shorter four-equation form of the aperture measures (App. C, Eqs. MapTrafo4_1-4), a
+ * cross-check of the eight-equation form: from <M^3>(t1,t2,t3) and the one-conjugate correlator
+ * at three orderings of the radii. The printed equations place the conjugate on the last radius of
+ * each ordering; this library's <M^* M^2> (Gamma_1 with F_1) conjugates the first, so they are
+ * evaluated at (t3,t1,t2), (t2,t1,t3) and (t1,t2,t3). Output d_m4 [n_z^3][n_ap][4] double:
+ * Map^3, <Map Map Mx>, <Map Mx Mx>, Mx^3 at (t1,t2,t3). It agrees with mp3pcf_to_map3 where the
+ * estimated correlators obey the relabelling symmetries the appendix uses (to the quadrature and
+ * binning of the 3PCF). n_ap <= 21845; the context holds the scratch. */
+mp3pcf_status mp3pcf_to_map3_four(mp3pcf_ctx* ctx, const double* d_gamma_cen, int64_t n_ap,
+                                  const double* d_theta_ap, double* d_m4);
 
 /* ---- Grid-based approximation (Sec. 3.2): the pixel catalog of a regular grid. Pixel (ix, iy)
  * of z-bin z covers [origin[0] + ix * pixel_q, origin[0] + (ix + 1) * pixel_q) x (the same in y),

@@ -216,6 +216,18 @@ class Estimator:
                                                  _ptr(corr), _ptr(m8)), "mp3pcf_to_map3", self._ctx)
         return corr, m8
 
+    def to_map3_four(self, gamma_cen, theta_ap):
+        """m4 [n_z^3][n_ap][4] = (Map^3, <Map^2 Mx>, <Map Mx^2>, <Mx^3>) by the four-equation form
+        of App. C (mp3pcf_to_map3_four), a cross-check of to_map3's eight-equation form."""
+        torch = _torch()
+        th = torch.as_tensor(np.atleast_2d(np.asarray(theta_ap, dtype=np.float64)),
+                             device=self.device).contiguous()
+        n_ap = th.shape[0]
+        m4 = torch.empty((self.z3, n_ap, 4), dtype=torch.float64, device=self.device)
+        native.check(native.lib().mp3pcf_to_map3_four(self._ctx, _ptr(gamma_cen), n_ap, _ptr(th), _ptr(m4)),
+                     "mp3pcf_to_map3_four", self._ctx)
+        return m4
+
     # ------------------------------------------------------------------ batching
     def set_extent(self, extent):
         """Fixed patch extent (x0, y0, x1, y1) in position quanta, or None."""

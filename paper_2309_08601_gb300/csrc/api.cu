@@ -371,7 +371,7 @@ struct mp3pcf_ctx {
     DevBuf d_e2q, d_edges, d_nodes;
     DevBuf bb, key, count, fill, scan_sums, scan_total, perm, pos, pay, zs;
     DevBuf cflag, crank, oflag, orank, centre_idx, crow;
-    DevBuf G, W, pairs, partial, singular, m3partial, ccoef;
+    DevBuf G, W, pairs, partial, singular, m3partial, m3four, ccoef;
     DevBuf gG, gW, gv, gtab, adjscratch;  // adjoint workspace
     DevBuf degen;                       // exclude_degenerate sums per (centre, z, bin)
     DevBuf degen_grad;                  // their gradient sums per (Z1, z, bin) in the adjoint
@@ -540,7 +540,7 @@ mp3pcf_status mp3pcf_create(const mp3pcf_config* cfg, void* stream, mp3pcf_ctx**
     if (ctx->d_e2q.ensure(sizeof(long long) * (nb + 1)) != cudaSuccess ||
         ctx->d_edges.ensure(sizeof(double) * (nb + 1)) != cudaSuccess ||
         ctx->d_nodes.ensure(sizeof(double) * nb) != cudaSuccess ||
-        ctx->bb.ensure(sizeof(int) * 8) != cudaSuccess || ctx->pairs.ensure(16) != cudaSuccess ||
+        ctx->bb.ensure(sizeof(int) * 8) != cudaSuccess || ctx->pairs.ensure(24) != cudaSuccess ||
         ctx->singular.ensure(8) != cudaSuccess)
         return cleanup(MP3PCF_ENOMEM);
     if (cudaMemcpy(ctx->d_e2q.p, ctx->e2q.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -560,7 +560,7 @@ mp3pcf_status mp3pcf_destroy(mp3pcf_ctx* ctx)
                       &ctx->pos, &ctx->pay, &ctx->zs, &ctx->cflag,
                       &ctx->crank, &ctx->oflag, &ctx->orank, &ctx->centre_idx, &ctx->crow,
                       &ctx->G, &ctx->W, &ctx->pairs, &ctx->partial, &ctx->singular,
-                      &ctx->m3partial, &ctx->ccoef, &ctx->gG, &ctx->gW, &ctx->gv, &ctx->gtab,
+                      &ctx->m3partial, &ctx->m3four, &ctx->ccoef, &ctx->gG, &ctx->gW, &ctx->gv, &ctx->gtab,
                       &ctx->adjscratch, &ctx->degen, &ctx->degen_grad, &ctx->zrange, &ctx->gridsum, &ctx->gridflag, &ctx->bups, &ctx->bnorm,
                       &ctx->bgam, &ctx->bgcen, &ctx->berr, &ctx->pix, &ctx->pixinv};
     for (DevBuf* b : bufs) b->release();
@@ -622,7 +622,7 @@ static mp3pcf_status accumulate_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq,
     ctx->n = n;
     ctx->n_centres = 0;
     ctx->combined = false;
-    MP3_CK(cudaMemsetAsync(ctx->pairs.p, 0, 16, st));
+    MP3_CK(cudaMemsetAsync(ctx->pairs.p, 0, 24, st));
     if (n == 0) return MP3PCF_OK;
     if (ctx->inject_alloc_failure) return fail(ctx, MP3PCF_ENOMEM, "injected allocation failure");
 
@@ -747,6 +747,7 @@ static mp3pcf_status accumulate_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq,
     a.G = ctx->G.as<cx<T>>() + b_lo;
     a.W = ctx->W.as<cx<T>>() + b_lo;
     a.pairs = ctx->pairs.as<unsigned long long>();
+    a.queue = ctx->pairs.as<unsigned long long>() + 2;
     if (b_lo >= b_hi) return MP3PCF_OK;
     cudaError_t e;
     {
@@ -1025,7 +1026,7 @@ mp3pcf_status mp3pcf_edge_correct(mp3pcf_ctx* ctx, const double* d_upsilon, cons
 mp3pcf_status mp3pcf_to_gamma(mp3pcf_ctx* ctx, const double* d_gamma_n, int32_t projection,
                               double* d_gamma_phi)
 {
-    if (!ctx || !d_gamma_n || !d_gamma_phi || (projection != 0 && projection != 1))
+    if (!ctx || !d_gamma_n || !d_gamma_phi || projection < 0 || projection > 2)
         return fail(ctx, MP3PCF_EINVAL, "bad argument");
     ctx->err.clear();
     StageScope sc(ctx, ST_GAMMA);
@@ -1049,6 +1050,26 @@ mp3pcf_status mp3pcf_to_map3(mp3pcf_ctx* ctx, const double* d_gamma_cen, int64_t
     ctx->launches[ST_MAP3] += 2;
     MP3_CK(launch_to_map3(post_args(ctx), d_gamma_cen, (int)n_ap, d_theta_ap,
                           ctx->m3partial.as<double>(), chunks, d_corr, d_m8, ctx->st));
+    return MP3PCF_OK;
+}
+
+mp3pcf_status mp3pcf_to_map3_four(mp3pcf_ctx* ctx, const double* d_gamma_cen, int64_t n_ap, const double* d_theta_ap,
+                                  double* d_m4)
+{
+    if (!ctx || !d_gamma_cen || n_ap < 0 || n_ap > 21845 || (n_ap > 0 && (!d_theta_ap || !d_m4)))
+        return fail(ctx, MP3PCF_EINVAL, "bad argument");
+    ctx->err.clear();
+    if (n_ap == 0) return MP3PCF_OK;
+    const mp3pcf_config& c = ctx->cfg;
+    const size_t z3 = (size_t)c.n_z * c.n_z * c.n_z;
+    const int chunks = 64;
+    MP3_CK(ctx->m3partial.ensure(sizeof(double) * 8 * z3 * 3 * n_ap * chunks));
+    MP3_CK(ctx->m3four.ensure(sizeof(double) * (9 * (size_t)n_ap + 24 * z3 * n_ap)));
+    StageScope sc(ctx, ST_MAP3);
+    ctx->launches[ST_MAP3] += 4;
+    double* theta3 = ctx->m3four.as<double>();
+    MP3_CK(launch_to_map3_four(post_args(ctx), d_gamma_cen, (int)n_ap, d_theta_ap, theta3, theta3 + 9 * n_ap,
+                               ctx->m3partial.as<double>(), chunks, d_m4, ctx->st));
     return MP3PCF_OK;
 }
 

@@ -93,6 +93,7 @@ struct MomentArgs {
     cx<T>* G;                   // [2 n_max + 3][n_centres][nz][nbp], offset to bin b_lo
     cx<T>* W;                   // [2 n_max + 1][n_centres][nz][nbp], offset to bin b_lo
     unsigned long long* pairs;  // [0] pair counter, [1] error flags (1: a bounded wait gave up)
+    unsigned long long* queue;  // centres claimed beyond the first gridDim.x (zero at launch)
 };
 
 // launchers implemented in moments_f32.cu / moments_f64.cu
@@ -171,6 +172,10 @@ cudaError_t launch_map3_direct(int64_t n, const int32_t* xq, const int32_t* yq, 
 cudaError_t launch_to_map3(const PostArgs& p, const double* gcen, int n_ap, const double* theta,
                            double* partial, int chunks, double* corr, double* m8,
                            cudaStream_t st);
+// the four-equation form: theta3 [3 n_ap][3] and corr3 [n_z^3][3 n_ap][4] complex are scratch,
+// partial as for launch_to_map3 with 3 n_ap apertures; m4 [n_z^3][n_ap][4]
+cudaError_t launch_to_map3_four(const PostArgs& p, const double* gcen, int n_ap, const double* theta, double* theta3,
+                                double* corr3, double* partial, int chunks, double* m4, cudaStream_t st);
 
 // ------------------------------------------------------------------ adjoint of stages (b), (a)
 

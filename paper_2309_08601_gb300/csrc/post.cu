@@ -365,10 +365,14 @@ __global__ void to_gamma_kernel(const PostArgs p, const double* __restrict__ gam
         cx<double> ep{1.0, 0.0};
         for (int n = 1; n <= nmax; ++n) {
             ep = cmul(ep, e1);
-            acc = cadd(acc, cmul(g0[(size_t)(nmax + n) * stride], ep));
-            acc = cadd(acc, cmul(g0[(size_t)(nmax - n) * stride], cconj(ep)));
+            cx<double> t = cadd(cmul(g0[(size_t)(nmax + n) * stride], ep),
+                                cmul(g0[(size_t)(nmax - n) * stride], cconj(ep)));
+            // projection 2: the average of e^{i n phi} over the angular bin is e^{i n phi_k}
+            // sinc(n pi / n_phi)
+            if (proj == 2) t = cscale(t, sinpi((double)n / np) / (M_PI * (double)n / np));
+            acc = cadd(acc, t);
         }
-        if (proj) acc = cmul(acc, centroid_factor((int)(zm % 4), p.nodes[b1], p.nodes[b2], e1));
+        if (proj == 1) acc = cmul(acc, centroid_factor((int)(zm % 4), p.nodes[b1], p.nodes[b2], e1));
         O[t] = acc;
     }
 }
@@ -632,6 +636,49 @@ cudaError_t launch_to_map3_adjoint(const PostArgs& p, int n_ap, const double* th
     if (blocks > 65535) blocks = 65535;
     if (blocks < 1) blocks = 1;
     map3_adjoint_kernel<<<(unsigned)blocks, 256, 0, st>>>(p, n_ap, theta, gcorr, gm8, ggcen);
+    return cudaGetLastError();
+}
+
+// ---- the four-equation form (App. C, Eqs. MapTrafo4_1-4). The printed equations put the
+// conjugate of each one-conjugate correlator on the last radius of its ordering (the convention of
+// the paper's reference for these forms); the library's Gamma_1 / F_1 correlator <M^* M^2>
+// conjugates the first, so A123, A132, A231 are <M^* M^2> at (t3, t1, t2), (t2, t1, t3) and
+// (t1, t2, t3); <M^3>(t1, t2, t3) comes with the last.
+__global__ void map3_orderings_kernel(int n_ap, const double* __restrict__ theta, double* __restrict__ theta3)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n_ap) return;
+    const double t1 = theta[3 * a], t2 = theta[3 * a + 1], t3 = theta[3 * a + 2];
+    double* o = theta3 + 9 * a;
+    o[0] = t3; o[1] = t1; o[2] = t2;
+    o[3] = t2; o[4] = t1; o[5] = t3;
+    o[6] = t1; o[7] = t2; o[8] = t3;
+}
+
+__global__ void map3_four_kernel(int jobs, const double* __restrict__ corr3, double* __restrict__ m4)
+{
+    const int job = blockIdx.x * blockDim.x + threadIdx.x;  // (Z-triplet, aperture)
+    if (job >= jobs) return;
+    const double* c = corr3 + (size_t)job * 3 * 8;  // [ordering][mu][re, im]
+    const double a1r = c[2], a1i = c[3], a2r = c[8 + 2], a2i = c[8 + 3], a3r = c[16 + 2], a3i = c[16 + 3];
+    const double mr = c[16], mi = c[17];
+    double* o = m4 + (size_t)job * 4;
+    o[0] = (a1r + a2r + a3r + mr) / 4.0;
+    o[1] = (-a1i + a2i + a3i + mi) / 4.0;
+    o[2] = (a1r + a2r - a3r - mr) / 4.0;
+    o[3] = (a1i + a2i + a3i - mi) / 4.0;
+}
+
+cudaError_t launch_to_map3_four(const PostArgs& p, const double* gcen, int n_ap, const double* theta, double* theta3,
+                                double* corr3, double* partial, int chunks, double* m4, cudaStream_t st)
+{
+    map3_orderings_kernel<<<(n_ap + 127) / 128, 128, 0, st>>>(n_ap, theta, theta3);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_to_map3(p, gcen, 3 * n_ap, theta3, partial, chunks, corr3, nullptr, st);
+    if (e != cudaSuccess) return e;
+    const int jobs = p.nz * p.nz * p.nz * n_ap;
+    map3_four_kernel<<<(jobs + 127) / 128, 128, 0, st>>>(jobs, corr3, m4);
     return cudaGetLastError();
 }
 

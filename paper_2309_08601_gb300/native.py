@@ -42,6 +42,7 @@ SIGNATURES = {
     "mp3pcf_edge_correct": ([P, P, P, P, P], C.c_int),
     "mp3pcf_to_gamma": ([P, P, I32, P], C.c_int),
     "mp3pcf_to_map3": ([P, P, I64, P, P, P], C.c_int),
+    "mp3pcf_to_map3_four": ([P, P, I64, P, P], C.c_int),
     "mp3pcf_map3_direct": ([P, I64, P, P, P, P, P, I64, P, I64, P, C.c_double, P], C.c_int),
     "mp3pcf_grid_catalog": ([P, I64, P, P, P, P, P, P, P, I64, I32, I32, P, P, P, P, P, P, P], C.c_int),
     "mp3pcf_accumulate_moments_combined": ([P, I64, P, P, P, P, P, P, P, I32, P, P], C.c_int),

@@ -93,6 +93,30 @@ def test_fp32_path_matches_oracle(gpu, orc, noise2k, noise_ref):
     print("fp32 errors", errs, "Map3 (pure noise, not gated):", rel_err(g["m8"], r.m8))
 
 
+def test_four_equation_form_matches_oracle(gpu, orc, noise2k, noise_ref):
+    """mp3pcf_to_map3_four (App. C, Eqs. MapTrafo4_1-4) against the oracle's four-equation form,
+    with equal and unequal radii (the orderings of the one-conjugate correlator differ only for
+    unequal ones)."""
+    import torch
+    s, r = noise_ref
+    th = [[2.0, 2.0, 2.0], [1.5, 2.5, 4.0], [4.0, 1.5, 2.5]]
+    want = orc.to_map3_four(s, r.gamma_cen, th)
+    with gpu.Estimator(**S0, precision="fp64") as est:
+        gc = torch.as_tensor(r.gamma_cen, device="cuda")
+        got = est.to_map3_four(gc, th).cpu().numpy()
+    assert rel_err(got, want) < 1e-10, rel_err(got, want)
+
+
+def test_bin_averaged_projection_matches_oracle(gpu, orc, noise2k, noise_ref):
+    """to_gamma projection 2 (the x-projection averaged over each angular bin) against the oracle."""
+    import torch
+    s, r = noise_ref
+    want = orc.to_gamma(s, r.gamma_n, 2)
+    with gpu.Estimator(**S0, precision="fp64") as est:
+        got = est.to_gamma(torch.as_tensor(r.gamma_n, device="cuda"), 2).cpu().numpy()
+    assert rel_err(got, want) < 1e-10, rel_err(got, want)
+
+
 def test_fp64_is_deterministic(gpu, noise2k):
     a = run(gpu, noise2k, S0, "fp64", stages="all")
     b = run(gpu, noise2k, S0, "fp64", stages="all")
