@@ -33,10 +33,19 @@
 // At n_max <= 30 (four warps) the FP32 kernel then holds 4 CTAs per SM: 128 registers per
 // thread and 57 KB of shared memory per CTA (with kMaxRows = 480).
 #ifndef MP3_MOM_SCR_F32
-#define MP3_MOM_SCR_F32 160  // candidates per warp and round (FP32)
+#define MP3_MOM_SCR_F32 160  // candidates per warp and round (FP32, <= 4 warps)
+#endif
+#ifndef MP3_MOM_SCR_F32_WIDE
+#define MP3_MOM_SCR_F32_WIDE 96  // the same for n_max >= 32 (six or more warps per CTA)
+#endif
+#ifndef MP3_MOM_FFMA2
+#define MP3_MOM_FFMA2 1  // FP32 sums through packed two-lane FMAs (n_max >= 32)
 #endif
 #ifndef MP3_MOM_MINB_F32
-#define MP3_MOM_MINB_F32 4  // CTAs per SM the FP32 register budget is sized for
+#define MP3_MOM_MINB_F32 4  // CTAs per SM the FP32 register budget is sized for (<= 4 warps)
+#endif
+#ifndef MP3_MOM_MINB_F32_WIDE
+#define MP3_MOM_MINB_F32_WIDE 3  // the same for n_max >= 32 (six or more warps per CTA)
 #endif
 
 namespace mp3 {
@@ -60,7 +69,8 @@ struct MomPlan {
     static constexpr int P0 = (NM + MomTraits<T>::kPerPart - 1) / MomTraits<T>::kPerPart;
     static constexpr int P = P0 > 8 ? 8 : P0;  // warps = order residue classes
     static constexpr int NT = 32 * P;
-    static constexpr int SCR = MomTraits<T>::kScr;  // candidates per warp and round
+    static constexpr bool WIDE = P > 4;
+    static constexpr int SCR = sizeof(T) == 4 && WIDE ? MP3_MOM_SCR_F32_WIDE : MomTraits<T>::kScr;  // per warp and round
     static_assert(SCR % 32 == 0, "whole batches");
     static constexpr int CH = P * SCR;                // chunk capacity (members)
     static constexpr int NWM = (2 * NMAX) / P + 1;   // W orders of warp 0
@@ -68,7 +78,12 @@ struct MomPlan {
     static constexpr int NA = 4 * NABM + 2 * NWM;    // scalar accumulators
     static constexpr int NAP = (NA + 31) / 32 * 32;  // padded for the reduce-scatter
     static constexpr int MINB_R = 65536 / (NT * 112) > 0 ? 65536 / (NT * 112) : 1;
-    static constexpr int MINB = sizeof(T) == 4 ? (MP3_MOM_MINB_F32 < MINB_R ? MP3_MOM_MINB_F32 : MINB_R) : 1;
+    static constexpr int MINB_F = WIDE ? MP3_MOM_MINB_F32_WIDE : MP3_MOM_MINB_F32;
+    static constexpr int MINB = sizeof(T) == 4 ? (MINB_F < MINB_R ? MINB_F : MINB_R) : 1;
+    // packed FP32 FMAs: measured faster with six or more warps per CTA (fewer CTAs per SM, the
+    // FMA pipe the limit while consuming) and 2.5 % slower with four (issue slots to spare)
+    static constexpr bool PACKED = sizeof(T) == 4 && WIDE && MP3_MOM_FFMA2 != 0;
+
 };
 
 template <typename T, int P, int SCR>
@@ -83,6 +98,7 @@ struct MomSmem {
     long long e2q[kMaxBins + 1];
     int cnt[8];   // members in each warp's region this round
     int wtot[8];  // per-warp partial sums of the prefix scan
+    int claim;    // the CTA's next centre from the work queue
 };
 
 template <typename T, int NMAX>
@@ -200,7 +216,7 @@ __device__ __forceinline__ void warp_reduce_scatter(T (&v)[N], int lane)
 // order recurrence c_{j+1} = kappa c_j - c_{j-1} (kappa = 2 cos(P phi)) over the warp's orders.
 // flatten() writes them as NAP scalars, in the order the reduce-scatter expects
 // (A_j.re, A_j.im, B_j.re, B_j.im for j < NABM, then W_j.re, W_j.im).
-template <typename T, int NABM, int NWM>
+template <typename T, int NABM, int NWM, bool PACKED>
 struct MomAcc {
     cx<T> a[NABM], b[NABM], w[NWM];
 
@@ -263,7 +279,7 @@ struct MomAcc {
 // multiplied by s_j in flatten(). Negation is exact, so the results are bit-identical to the
 // scalar form above.
 template <int NABM, int NWM>
-struct MomAcc<float, NABM, NWM> {
+struct MomAcc<float, NABM, NWM, true> {
     float2 a[NABM], b[NABM], w[NWM];
 
     __device__ __forceinline__ void reset()
@@ -350,8 +366,12 @@ __global__ void __launch_bounds__(MomPlan<T, NMAX>::NT, MomPlan<T, NMAX>::MINB) 
     for (int i = tid; i <= nb; i += NT) s.e2q[i] = A.e2q[i];
     __syncthreads();
 
-    MomAcc<T, NABM, NWM> macc;
-    for (int c = blockIdx.x; c < A.n_centres; c += gridDim.x) {
+    MomAcc<T, NABM, NWM, PL::PACKED> macc;
+    // Centres come from a work queue: a CTA starts with centre blockIdx.x and then claims the next
+    // unprocessed one (one atomic per centre), so CTAs whose centres have fewer neighbours (masked
+    // regions, patch edges, sparse z-bins) take more of them and all finish together. A centre's
+    // result does not depend on the CTA that computes it.
+    for (int c = blockIdx.x; c < A.n_centres;) {
         const int2 pc = A.pos[A.centre_idx[c]];
         const float fx = (float)((long long)pc.x - A.g.x0);
         const float fy = (float)((long long)pc.y - A.g.y0);
@@ -503,21 +523,20 @@ __global__ void __launch_bounds__(MomPlan<T, NMAX>::NT, MomPlan<T, NMAX>::MINB) 
                         const int cnt = s.cnt[w2];
                         my_pairs += (unsigned long long)cnt;
                         const int e0 = w2 * SCR;
+                        // orders m_j = warp + j P. With |z| = 1, z^{m+P} + z^{m-P} =
+                        // 2 cos(P phi) z^m, so c_{j+1} = kappa c_j - c_{j-1}, kappa = 2 Re(z^P),
+                        // real and imaginary parts alike. The recurrence runs at most NWM - 2
+                        // steps, so its rounding error stays within a few hundred ulp of the
+                        // directly multiplied power.
                         for (int e = e0 + lane; e < e0 + cnt; e += 32) {
                             const cx<T> zP = lds_cx(aP + e * (uint32_t)sizeof(cx<T>), T(0));
                             const cx<T> zq = lds_cx(aq + e * (uint32_t)sizeof(cx<T>), T(0));
                             const cx<T> abv = lds_cx(ab_base + e * (uint32_t)sizeof(cx<T>), T(0));
-                            const T av = abv.x, bv = abv.y;
                             const T wv = lds_r(w_base + e * (uint32_t)sizeof(T), T(0));
-                            // orders m_j = warp + j P. With |z| = 1, z^{m+P} + z^{m-P} =
-                            // 2 cos(P phi) z^m, so c_{j+1} = kappa c_j - c_{j-1}, kappa = 2 Re(z^P),
-                            // real and imaginary parts alike. The recurrence runs at most NWM - 2
-                            // steps, so its rounding error stays within a few hundred ulp of the
-                            // directly multiplied power.
                             const T kappa = zP.x + zP.x;
                             const cx<T> c0 = warp == 0 ? cx<T>{T(1), T(0)} : zq;
                             const cx<T> c1 = warp == 0 ? zP : cmul(zq, zP);
-                            macc.add(av, bv, wv, kappa, c0, c1, lastAB, lastW);
+                            macc.add(abv.x, abv.y, wv, kappa, c0, c1, lastAB, lastW);
                         }
                     }
                     __syncthreads();  // the chunk may be overwritten
@@ -548,6 +567,9 @@ __global__ void __launch_bounds__(MomPlan<T, NMAX>::NT, MomPlan<T, NMAX>::MINB) 
                 __syncwarp();
             }
         }
+        if (tid == 0) s.claim = (int)min(atomicAdd(A.queue, 1ull) + gridDim.x, (unsigned long long)A.n_centres);
+        __syncthreads();
+        c = s.claim;
     }
     if (tid == 0 && my_pairs) atomicAdd(A.pairs, my_pairs);
 }

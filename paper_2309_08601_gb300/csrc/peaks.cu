@@ -2,8 +2,8 @@
 // service for rooflines; the paper has no counterpart). Each probe fills every SM with warps that
 // run independent chains of one instruction kind on register operands, so the pipe, not latency
 // or memory, limits it: FP32 fused multiply-add (one lane per instruction), the packed two-lane
-// FP32 FMA of sm_100 and later (__ffma2_rn), and FP64 FMA. The effective SM clock of the run is
-// measured alongside (clock64 cycles of one block over the event time).
+// FP32 FMA of sm_100 and later (__ffma2_rn), and FP64 FMA. The SM clock of the run is measured
+// alongside: one block's clock64 cycles over the global timer's nanoseconds for the same span.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,6 +22,8 @@ __global__ void __launch_bounds__(kThreads) probe_kernel(float mf, float af, dou
                                                          float* sink, long long* cycles)
 {
     const long long t0 = clock64();
+    unsigned long long g0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(g0));
     if constexpr (KIND == 0) {
         float v[kChains];
 #pragma unroll
@@ -60,7 +62,13 @@ __global__ void __launch_bounds__(kThreads) probe_kernel(float mf, float af, dou
         for (int c = 0; c < kChains; ++c) s += v[c];
         if (s == -1.0) sink[threadIdx.x] = (float)s;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *cycles = clock64() - t0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const long long t1 = clock64();
+        unsigned long long g1;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(g1));
+        cycles[0] = t1 - t0;
+        cycles[1] = (long long)(g1 - g0);
+    }
 }
 
 template <int KIND>
@@ -118,7 +126,7 @@ extern "C" mp3pcf_status mp3pcf_measure_peak(int32_t kind, void* stream, double*
     float* sink = nullptr;
     long long* cyc = nullptr;
     if (cudaMalloc(&sink, sizeof(float) * peaks::kThreads) != cudaSuccess) return MP3PCF_ENOMEM;
-    if (cudaMalloc(&cyc, sizeof(long long)) != cudaSuccess) {
+    if (cudaMalloc(&cyc, 2 * sizeof(long long)) != cudaSuccess) {
         cudaFree(sink);
         return MP3PCF_ENOMEM;
     }
@@ -127,16 +135,15 @@ extern "C" mp3pcf_status mp3pcf_measure_peak(int32_t kind, void* stream, double*
     e = kind == 0 ? peaks::run<0>(grid, iters, st, sink, cyc, &ms)
         : kind == 1 ? peaks::run<1>(grid, iters, st, sink, cyc, &ms)
                     : peaks::run<2>(grid, iters, st, sink, cyc, &ms);
-    long long cycles = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&cycles, cyc, sizeof(long long), cudaMemcpyDeviceToHost);
+    long long cycles[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(cycles, cyc, sizeof(cycles), cudaMemcpyDeviceToHost);
     cudaFree(sink);
     cudaFree(cyc);
     if (e != cudaSuccess) return MP3PCF_ECUDA;
     // FMAs per thread: chains x steps, two lanes each for the packed form; 2 flops per FMA
     const double fmas = (double)grid * peaks::kThreads * peaks::kChains * iters * (kind == 1 ? 2.0 : 1.0);
     *h_flops_per_s = 2.0 * fmas / (ms * 1e-3);
-    // one block's cycles against its share of the launch time (the waves run back to back): an
-    // estimate of the SM clock during the probe, reported for the record
-    if (h_sm_mhz) *h_sm_mhz = (double)cycles * waves / (ms * 1e3);
+    // cycles per nanosecond of one block of the last launch
+    if (h_sm_mhz) *h_sm_mhz = cycles[1] > 0 ? 1e3 * (double)cycles[0] / (double)cycles[1] : 0.0;
     return MP3PCF_OK;
 }
