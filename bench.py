@@ -417,6 +417,63 @@ def run_reference(args):
     return 0
 
 
+def run_oracle_plan(args):
+    """The oracle's timing plan on the host cores (part of the reference arm): every workload on a
+    random centre sample (all galaxies as neighbours; the whole uniform_noise_2k catalog), with
+    all cores and with one, median of three runs each; pairs/s, and the seconds a whole catalog
+    would take extrapolated by pairs (the whole-catalog pair count estimated from the sample,
+    which is a uniform random subset of the centres). Prints one JSON line per workload."""
+    import oracle
+    from paper_2309_08601_gb300 import synth
+    oracle.build_oracle()
+    threads = oracle.num_threads()
+    plan = [("uniform_noise_2k", None), ("lognormal_200k", 6.0), ("masked_lognormal_1m", 6.0),
+            ("grad_lognormal_500k", 6.0), ("tomo_64x5_lognormal", 6.0)]
+    for name, target in plan:
+        p = synth.WORKLOADS[name]
+        if name == "tomo_64x5_lognormal":
+            cat = synth.make_tomographic_catalog(1000, side=p["side"], n_z=p["n_z"])
+            setup = dict(n_bins=p["n_bins"], theta_min=p["theta_min"], theta_max=p["theta_max"],
+                         n_max=p["n_max"], n_z=p["n_z"])
+        else:
+            cat = synth.workload_catalog(name)
+            setup = dict(n_bins=p["n_bins"], theta_min=p["theta_min"], theta_max=p["theta_max"], n_max=p["n_max"])
+        theta = [[t, t, t] for t in p["theta_ap"]]
+        s = oracle.Setup(**setup)
+        row = {"workload": name, "n_galaxies": int(cat.n), "cpu_model": cpu_model()}
+        for nt in (threads, 1):
+            oracle.set_num_threads(nt)
+            rates = []
+            for rep in range(3):
+                rng = np.random.default_rng(100 + rep)
+                if target is None:
+                    cen = np.arange(cat.n)
+                else:
+                    # size the sample for about target seconds (one core: half of it)
+                    order = rng.permutation(cat.n)
+                    probe = np.sort(order[:max(2, 2 * nt)])
+                    t0 = time.perf_counter()
+                    oracle.pipeline(s, cat, theta, probe)
+                    per = max(time.perf_counter() - t0, 1e-3) / probe.size
+                    k = int(np.clip((target if nt > 1 else target / 2) / per, 2, cat.n))
+                    cen = np.sort(order[:k])
+                pairs = oracle.count_pairs(s, cat, cen)
+                t0 = time.perf_counter()
+                oracle.pipeline(s, cat, theta, cen)
+                sec = time.perf_counter() - t0
+                rates.append((pairs / sec, pairs, cen.size, sec))
+            rates.sort()
+            rate, pairs, k, sec = rates[1]
+            full_pairs = pairs * cat.n / k
+            row["cores_%d" % nt] = {"pairs_per_s": rate, "centres_sampled": int(k), "sample_seconds": sec,
+                                    "catalog_seconds": full_pairs / rate,
+                                    "catalog_seconds_kind": "measured" if k == cat.n else "extrapolated by pairs"}
+        row["pairs_per_catalog_estimate"] = float(full_pairs)
+        oracle.set_num_threads(threads)
+        print(json.dumps(row), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ multi-rank host logic
 
 def rank_seed(seed: int, rank: int) -> int:
@@ -769,7 +826,11 @@ def main(argv=None):
     ap.add_argument("--no-combined", dest="combined", action="store_false",
                     help="skip the combined-versus-discrete estimator timing")
     ap.add_argument("--ref-step-s", type=float, default=8.0)
+    ap.add_argument("--oracle-plan", action="store_true",
+                    help="with --impl reference: the oracle's timing plan over every workload")
     args = ap.parse_args(argv)
+    if args.impl == "reference" and args.oracle_plan:
+        return run_oracle_plan(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -151,18 +151,36 @@ def test_homogeneity_identities_lognormal(gpu, precision, tol):
     assert abs(ew) <= tol * ew_abs
 
 
-def test_finite_differences_5000(gpu, orc):
-    """C4 model at N = 5000 (same patch, 100x lower density): FP64 forward central differences
-    (h = 1e-4) on 100 random galaxies against the FP32 and FP64 adjoints, and the whole FP64
-    gradient against the oracle's FP64 autograd. At this density the 0.5' bins hold ~0.02 pairs
-    per galaxy, so most small-scale edge-correction systems are nearly singular and the solution
-    (and its gradient) is ill-conditioned there; the check therefore keeps the C4 patch, model,
-    n_max and bin count but starts the 20 log bins at 10' (every (b1, b2) system well filled)."""
-    from oracle import torch_oracle as to
+def _c4_density_case():
+    """The differentiation workload's density (5e5 galaxies on 420') on a 42' patch of 5000
+    galaxies, with the first 12 of its 20 log bins (0.5'-13.4', the same edges), so that its
+    small-scale systems are filled as at full size (~1.6 pairs per galaxy in the 0.5' bin)."""
+    p = synth.WORKLOADS["grad_lognormal_500k"]
+    ratio = (p["theta_max"] / p["theta_min"]) ** (1.0 / p["n_bins"])
+    side = p["side"] * np.sqrt(5000 / p["n"])
+    cat = synth.make_catalog(5000, side, p["seed"], field=p["field"], weights=p["weights"])
+    setup = dict(n_bins=12, theta_min=p["theta_min"], theta_max=p["theta_min"] * ratio ** 12, n_max=p["n_max"])
+    return cat, setup, [[2.0, 2.0, 2.0], [4.0, 4.0, 4.0]]
+
+
+def _c4_patch_case():
+    """The differentiation workload's patch and model at 100x lower density (5000 galaxies on
+    420'): the 0.5' bins would hold ~0.02 pairs per galaxy and their edge-correction systems be
+    nearly singular, so the 20 log bins start at 10' (every (b1, b2) system well filled)."""
     p = synth.WORKLOADS["grad_lognormal_500k"]
     cat = synth.make_catalog(5000, p["side"], p["seed"], field=p["field"], weights=p["weights"])
     setup = dict(n_bins=p["n_bins"], theta_min=10.0, theta_max=p["theta_max"], n_max=p["n_max"])
-    th = [[t, t, t] for t in p["theta_ap"]]
+    return cat, setup, [[t, t, t] for t in p["theta_ap"]]
+
+
+@pytest.mark.parametrize("case", ["c4_density_small_bins", "c4_patch_large_bins"])
+def test_finite_differences_5000(gpu, orc, case):
+    """5000 galaxies of the differentiation workload's model, n_max 30: FP64 forward central
+    differences (h = 1e-4) on 100 random galaxies against the FP32 and FP64 adjoints, and the whole
+    FP64 gradient against the oracle's FP64 autograd; once at the workload's density with its own
+    small-scale bins, once on its whole patch with bins from 10'."""
+    from oracle import torch_oracle as to
+    cat, setup, th = _c4_density_case() if case == "c4_density_small_bins" else _c4_patch_case()
     c = np.zeros((1, len(th), 8))
     c[0, :, 0] = 1.0  # L = sum of Map^3 over the apertures
     dev = gpu.catalog_to_device(cat)
