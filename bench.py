@@ -55,10 +55,14 @@ HBM_PEAK_GBS, HBM_PEAK_NOTE = _measured_hbm_gbs()
 # the same density (the traffic of both kernels is proportional to the centres); None until the
 # kernel has been captured since its last change.
 TRAFFIC_BYTES = {
-    ("moments", "masked_lognormal_1m"): None,
+    # moments_kernel<float,40>: capture at 100 000 galaxies of the same density, x10
+    # (profiles/moments_kernel_masked_lognormal_100k.md)
+    ("moments", "masked_lognormal_1m"): 10 * (630.813440e6 + 4.473916e9),
     ("moments", "lognormal_200k"): None,
-    ("contract", "masked_lognormal_1m"): None,
-    ("contract", "lognormal_200k"): None,
+    # contract_tc_kernel<Bf16Split>: captures at 50 000 galaxies of each density, x20 and x4
+    # (profiles/contract_tc_bf16x3_traffic_50k.md)
+    ("contract", "masked_lognormal_1m"): 20 * (2.296950784e9 + 20.345856e6),
+    ("contract", "lognormal_200k"): 4 * (1.076729856e9 + 8.673792e6),
 }
 TRAFFIC_NOTE = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (profiles/)"
 
@@ -287,14 +291,19 @@ def measure_batch(api, n_real: int, precision: str, stream, fp64_frac: float):
             with api.Estimator(**bset, precision=prec, stream=stream) as e:
                 e.measure(*d0[:5], theta_ap=bth, zbin=d0[5], centre_mask=sel, report_singular=False)
                 torch.cuda.synchronize()
+                e.set_timing(True)
+                e.stage_times(reset=True)
                 a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a0.record(stream)
                 m = e.measure(*d0[:5], theta_ap=bth, zbin=d0[5], centre_mask=sel, report_singular=False)
                 a1.record(stream)
                 torch.cuda.synchronize()
-                res[prec] = (a0.elapsed_time(a1) / 1e3, e.counts()[1], m.m8.cpu().numpy())
-        s64, p64, m64 = res["fp64"]
-        sp, _, mp = res[precision]
+                st = e.stage_times(reset=True)
+                e.set_timing(False)
+                res[prec] = (a0.elapsed_time(a1) / 1e3, e.counts()[1], m.m8.cpu().numpy(),
+                             {k: v[0] for k, v in st.items()})
+        s64, p64, m64, _ = res["fp64"]
+        sp, _, mp, stp = res[precision]
         frac = p64 / pairs_each[0]
         fp64_cat_s = frac / s64  # realisations per second, extrapolated by pairs
         auto = np.zeros(m64.shape[0], bool)
@@ -308,19 +317,24 @@ def measure_batch(api, n_real: int, precision: str, stream, fp64_frac: float):
             "precision_over_fp64_same_subset": s64 / sp,
             "batched_over_fp64_catalogs_per_s": (n_real / sec) / fp64_cat_s,
             "map3_rel_err_vs_fp64_auto_triplets": float(np.abs(mp[auto, :, 0] - m64[auto, :, 0]).max() /
-                                                        np.abs(m64[auto, :, 0]).max())}
+                                                        np.abs(m64[auto, :, 0]).max()),
+            "precision_stage_ms_on_subset": stp,
+            "contraction_over_moments": stp["contract"] / max(stp["moments"], 1e-9)}
     return out
 
 
-def measure_combined(api, precision: str, stream):
-    """The combined estimator (Sec. 3.3) against the discrete one on the multiscale_310k workload
-    (the density and binning of the paper's accuracy test of it, a tenth of its area): moments and
-    contraction of each, timed with CUDA events after one untimed run; the levels start at 20
-    pixels of 0.25' and double the pixel every octave, as in that test."""
+def measure_combined(api, precision: str, stream, name: str = "multiscale_310k"):
+    """The combined estimator (Sec. 3.3) against the discrete one on a noise-free multi-scale
+    workload (the density and binning of the paper's accuracy test of it: multiscale_310k on a
+    tenth of its area, multiscale_3m on all of it): moments and contraction of each, timed with
+    CUDA events after one untimed run; the levels start at 20 pixels of 0.25' and double the pixel
+    every octave, as in that test. Differences: the multipoles norm-wise over every block with a
+    grid bin, and the centroid-projected Gamma_0 on the equilateral grid bins, per bin the largest
+    difference over phi relative to the largest |Gamma_0| (the measure of the paper's figure)."""
     import torch
     from paper_2309_08601_gb300 import synth
-    p = synth.WORKLOADS["multiscale_310k"]
-    cat = synth.workload_catalog("multiscale_310k")
+    p = synth.WORKLOADS[name]
+    cat = synth.workload_catalog(name)
     dev = api.catalog_to_device(cat)
     cset = dict(n_bins=p["n_bins"], theta_min=p["theta_min"], theta_max=p["theta_max"], n_max=p["n_max"])
     with api.Estimator(**cset, precision=precision, stream=stream) as ec:
@@ -343,12 +357,16 @@ def measure_combined(api, precision: str, stream):
             ups, norm = run(combined)
             t1.record(stream)
             torch.cuda.synchronize()
-            out[combined] = (t0.elapsed_time(t1), ec.counts()[1], ups.cpu().numpy(), norm.cpu().numpy())
+            gam, _ = ec.edge_correct(ups, norm, report_singular=False)
+            g0 = ec.to_gamma(gam, 1)[0, 0].cpu().numpy()
+            out[combined] = (t0.elapsed_time(t1), ec.counts()[1], ups.cpu().numpy(), norm.cpu().numpy(), g0)
     b0 = levels[0][0]
     nb = p["n_bins"]
     grid = np.zeros((nb, nb), bool)
     grid[b0:, :] = grid[:, b0:] = True
     ud, nd, uc, nc = out[False][2], out[False][3], out[True][2], out[True][3]
+    gd, gcm = out[False][4], out[True][4]
+    eq = [float(np.abs(gcm[b, b] - gd[b, b]).max() / np.abs(gd[b, b]).max()) for b in range(b0, nb)]
 
     def nerr(a, b):
         return float(np.linalg.norm(a - b) / np.linalg.norm(b))
@@ -360,6 +378,9 @@ def measure_combined(api, precision: str, stream):
             "discrete_pairs": int(out[False][1]), "combined_pairs": int(out[True][1]),
             "grid_blocks_rel_err_upsilon_n_le_10": nerr(uc[:, :, :11][..., grid], ud[:, :, :11][..., grid]),
             "grid_blocks_rel_err_norm_n_le_20": nerr(nc[:, :21][..., grid], nd[:, :21][..., grid]),
+            "grid_blocks_rel_err_upsilon_n_le_3": nerr(uc[:, :, :4][..., grid], ud[:, :, :4][..., grid]),
+            "equilateral_gamma0_rel_err_median": float(np.median(eq)),
+            "equilateral_gamma0_rel_err_max": float(np.max(eq)),
             "discrete_block_rel_err": float(np.abs(uc[..., ~grid] - ud[..., ~grid]).max() /
                                             np.abs(ud[..., ~grid]).max())}
 
@@ -418,11 +439,13 @@ def run_reference(args):
 
 
 def run_oracle_plan(args):
-    """The oracle's timing plan on the host cores (part of the reference arm): every workload on a
-    random centre sample (all galaxies as neighbours; the whole uniform_noise_2k catalog), with
-    all cores and with one, median of three runs each; pairs/s, and the seconds a whole catalog
-    would take extrapolated by pairs (the whole-catalog pair count estimated from the sample,
-    which is a uniform random subset of the centres). Prints one JSON line per workload."""
+    """The oracle's timing plan on the host cores (part of the reference arm). Per workload: the
+    pair-proportional part of the path (moments and contraction) on a random centre sample (all
+    galaxies as neighbours; the whole uniform_noise_2k catalog), with all cores and with one,
+    median of three runs, giving pairs/s; and the per-catalog post-processing (edge correction,
+    Gamma, aperture measures), timed once with all cores and once with one. A whole catalog's
+    seconds = its pairs / that rate + the post-processing, the pairs estimated from the sample
+    (a uniform random subset of the centres). Prints one JSON line per workload."""
     import oracle
     from paper_2309_08601_gb300 import synth
     oracle.build_oracle()
@@ -441,6 +464,13 @@ def run_oracle_plan(args):
         theta = [[t, t, t] for t in p["theta_ap"]]
         s = oracle.Setup(**setup)
         row = {"workload": name, "n_galaxies": int(cat.n), "cpu_model": cpu_model()}
+
+        def pair_part(cen):
+            t0 = time.perf_counter()
+            G, W = oracle.moments(s, cat, cen)
+            ups, norm = oracle.contract(s, cat, G, W, cen)
+            return time.perf_counter() - t0, ups, norm
+
         for nt in (threads, 1):
             oracle.set_num_threads(nt)
             rates = []
@@ -452,21 +482,22 @@ def run_oracle_plan(args):
                     # size the sample for about target seconds (one core: half of it)
                     order = rng.permutation(cat.n)
                     probe = np.sort(order[:max(2, 2 * nt)])
-                    t0 = time.perf_counter()
-                    oracle.pipeline(s, cat, theta, probe)
-                    per = max(time.perf_counter() - t0, 1e-3) / probe.size
+                    per = max(pair_part(probe)[0], 1e-3) / probe.size
                     k = int(np.clip((target if nt > 1 else target / 2) / per, 2, cat.n))
                     cen = np.sort(order[:k])
                 pairs = oracle.count_pairs(s, cat, cen)
-                t0 = time.perf_counter()
-                oracle.pipeline(s, cat, theta, cen)
-                sec = time.perf_counter() - t0
+                sec, ups, norm = pair_part(cen)
                 rates.append((pairs / sec, pairs, cen.size, sec))
             rates.sort()
             rate, pairs, k, sec = rates[1]
             full_pairs = pairs * cat.n / k
+            t0 = time.perf_counter()
+            gam, _ = oracle.edge_correct(s, ups, norm)
+            gc = oracle.to_gamma(s, gam, 1)
+            oracle.to_map3(s, gc, theta)
+            post = time.perf_counter() - t0
             row["cores_%d" % nt] = {"pairs_per_s": rate, "centres_sampled": int(k), "sample_seconds": sec,
-                                    "catalog_seconds": full_pairs / rate,
+                                    "post_seconds": post, "catalog_seconds": full_pairs / rate + post,
                                     "catalog_seconds_kind": "measured" if k == cat.n else "extrapolated by pairs"}
         row["pairs_per_catalog_estimate"] = float(full_pairs)
         oracle.set_num_threads(threads)
@@ -503,11 +534,12 @@ def whole_job(units_per_step_all_ranks: float, steps: int, seconds_max: float) -
 # ------------------------------------------------------------------ GPU arm
 
 def measure_peaks(native):
-    """FP32 FMA (scalar and packed two-lane) and FP64 FMA throughput of this GPU, measured by the
-    library's probe (mp3pcf_measure_peak), in TFLOP/s, with the probe's SM clock estimate."""
+    """FP32 FMA (scalar and packed two-lane), FP64 FMA and tcgen05 BF16 / TF32 MMA throughput of
+    this GPU, measured by the library's probe (mp3pcf_measure_peak), in TFLOP/s, with the probe's
+    SM clock."""
     import ctypes as C
     out = {}
-    for kind, name in ((0, "fp32_fma"), (1, "fp32_ffma2"), (2, "fp64_fma")):
+    for kind, name in ((0, "fp32_fma"), (1, "fp32_ffma2"), (2, "fp64_fma"), (3, "bf16_tcgen05"), (4, "tf32_tcgen05")):
         f, mhz = C.c_double(0.0), C.c_double(0.0)
         native.check(native.lib().mp3pcf_measure_peak(kind, None, C.byref(f), C.byref(mhz)), "measure_peak")
         out[name + "_tflops"] = f.value / 1e12
@@ -595,7 +627,10 @@ def measure_fp64_subset(api, dev, n, setup, theta, pairs_full, precision, stream
 
 def oracle_parity(api, dev, cat, setup, theta, precision, stream, n_centres, seed=12):
     """The precision form against the FP64 oracle on a random sample of centres (all galaxies as
-    neighbours): normwise relative errors of Upsilon, N and the eight aperture measures."""
+    neighbours): normwise relative errors of Upsilon and N. The edge correction and what follows
+    are compared on the FP64 GPU path's subset instead (measure_fp64_subset): with a few dozen
+    centres most small-scale mode-coupling systems hold a handful of triplets, and their solution
+    amplifies any rounding without bound."""
     import torch
     import oracle
     rng = np.random.default_rng(seed)
@@ -609,15 +644,13 @@ def oracle_parity(api, dev, cat, setup, theta, precision, stream, n_centres, see
         m = e.measure(*dev[:5], theta_ap=theta, centre_mask=torch.as_tensor(mask, device="cuda"),
                       report_singular=False)
         torch.cuda.synchronize()
-        g = {"ups": m.upsilon.cpu().numpy(), "norm": m.norm.cpu().numpy(), "m8": m.m8.cpu().numpy()}
+        g = {"ups": m.upsilon.cpu().numpy(), "norm": m.norm.cpu().numpy()}
 
     def rel(a, b):
-        ok = np.isfinite(b)
-        return float(np.abs(a[ok] - b[ok]).max() / np.abs(b[ok]).max())
+        return float(np.abs(a - b).max() / np.abs(b).max())
 
     return {"centres": int(n_centres), "oracle_seconds": t_orc, "upsilon_rel_err": rel(g["ups"], r.ups),
-            "norm_rel_err": rel(g["norm"], r.norm), "m8_rel_err": rel(g["m8"], r.m8),
-            "map3_rel_err": rel(g["m8"][..., 0], r.m8[..., 0])}
+            "norm_rel_err": rel(g["norm"], r.norm)}
 
 
 def measure_workload(api, name, precision, stream, steps, warmup, seed_offset=0):
@@ -774,6 +807,8 @@ def run_gpu(args):
     # ---- the combined estimator against the discrete one (rank 0)
     if rank == 0 and args.combined:
         line["combined"] = measure_combined(api, args.precision, stream)
+    if rank == 0 and args.combined_full_area:
+        line["combined_full_area"] = measure_combined(api, args.precision, stream, "multiscale_3m")
 
     if rank == 0 and args.cpu_baseline:
         import oracle
@@ -825,6 +860,8 @@ def main(argv=None):
                     help="tomographic realisations timed through mp3pcf_run_batch (0: skip)")
     ap.add_argument("--no-combined", dest="combined", action="store_false",
                     help="skip the combined-versus-discrete estimator timing")
+    ap.add_argument("--combined-full-area", action="store_true",
+                    help="also the combined-versus-discrete comparison at the paper's full area (3.1e6 galaxies)")
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     ap.add_argument("--oracle-plan", action="store_true",
                     help="with --impl reference: the oracle's timing plan over every workload")

@@ -340,10 +340,12 @@ mp3pcf_status mp3pcf_stage_times(mp3pcf_ctx* ctx, double* h_ms, int64_t* h_launc
 
 /* Measurement service for rooflines (the paper has no counterpart). Runs, on the current device
  * and `stream`, a probe that keeps every SM busy with independent chains of one arithmetic
- * instruction: kind 0 FP32 FMA, 1 packed two-lane FP32 FMA (sm_100 and later), 2 FP64 FMA.
+ * instruction: kind 0 FP32 FMA, 1 packed two-lane FP32 FMA (sm_100 and later), 2 FP64 FMA; or
+ * with back-to-back tensor-core MMAs (tcgen05, M 128, N 256, FP32 accumulation in tensor
+ * memory): kind 3 BF16 inputs, 4 TF32 inputs (ETIMEOUT if their bounded completion wait gave up).
  * Returns the best of three timed launches (after one warm-up) in *h_flops_per_s (2 flops per
- * FMA) and an estimate of the SM clock during the probe in *h_sm_mhz (may be NULL). Allocates
- * and frees two small device buffers and synchronises the stream. EINVAL for another kind. */
+ * FMA) and the SM clock during the probe in *h_sm_mhz (may be NULL). Allocates and frees two
+ * small device buffers and synchronises the stream. EINVAL for another kind. */
 mp3pcf_status mp3pcf_measure_peak(int32_t kind, void* stream, double* h_flops_per_s, double* h_sm_mhz);
 
 /* Allocation-free form of mp3pcf_to_map3 (the paper has no counterpart: it is a service of this

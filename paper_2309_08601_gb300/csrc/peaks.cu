@@ -1,8 +1,9 @@
 // Throughput probes of the arithmetic pipes that bound this library's kernels (a measurement
-// service for rooflines; the paper has no counterpart). Each probe fills every SM with warps that
-// run independent chains of one instruction kind on register operands, so the pipe, not latency
-// or memory, limits it: FP32 fused multiply-add (one lane per instruction), the packed two-lane
-// FP32 FMA of sm_100 and later (__ffma2_rn), and FP64 FMA. The SM clock of the run is measured
+// service for rooflines; the paper has no counterpart). Each probe fills every SM with work that
+// only the probed pipe limits: independent chains of FP32 fused multiply-adds (one lane per
+// instruction), of the packed two-lane FP32 FMA of sm_100 and later (__ffma2_rn) and of FP64 FMAs
+// on register operands; and back-to-back tcgen05 tensor-core MMAs (BF16 and TF32 inputs, FP32
+// accumulation) on operands resident in shared memory. The SM clock of the run is measured
 // alongside: one block's clock64 cycles over the global timer's nanoseconds for the same span.
 #include <cuda_runtime.h>
 
@@ -71,6 +72,99 @@ __global__ void __launch_bounds__(kThreads) probe_kernel(float mf, float af, dou
     }
 }
 
+// ---- tensor-core probe: one thread per CTA issues back-to-back tcgen05.mma (M = 128, N = 256,
+// K = 16 BF16 or 8 TF32, FP32 accumulation in tensor memory) on operands resident in shared
+// memory (every element 1/64, so the accumulator stays small), commits to an mbarrier, and the
+// CTA waits for it (bounded, about a second) before freeing the tensor memory.
+constexpr int kMmaM = 128, kMmaN = 256;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t desc_noswizzle(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    // canonical K-major layout without swizzle: start, leading (K) and stride (M/N) offsets
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo & 0x3FFFF) >> 4) << 16;
+    d |= (uint64_t)((sbo & 0x3FFFF) >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+template <bool TF32>
+__global__ void __launch_bounds__(128, 1) mma_probe_kernel(int iters, unsigned long long* err, long long* cycles)
+{
+    __shared__ __align__(1024) uint32_t ops[3072];  // A: 128 rows x 32 B, B: 256 rows x 32 B
+    __shared__ uint32_t tmem_base;
+    __shared__ __align__(8) unsigned long long done;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t one64 = TF32 ? 0x3c800000u : 0x3c803c80u;  // 1/64 in FP32 / two BF16
+    for (int i = tid; i < 3072; i += 128) ops[i] = one64;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(kMmaN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&done)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const long long t0 = clock64();
+    if (tid == 0) {
+        constexpr uint32_t fmt = TF32 ? 2u : 1u;
+        const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kMmaN >> 3) << 17) |
+                               ((uint32_t)(kMmaM >> 4) << 24);
+        const uint64_t a = desc_noswizzle(smem_addr(ops), 128, 256);
+        const uint64_t b = desc_noswizzle(smem_addr(ops + 1024), 128, 256);
+        for (int i = 0; i < iters; ++i) {
+            const uint32_t acc = i > 0 ? 1u : 0u;
+            if constexpr (TF32)
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                             "l"(a), "l"(b), "r"(idesc), "r"(acc));
+            else
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                             "l"(a), "l"(b), "r"(idesc), "r"(acc));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_addr(&done))
+                     : "memory");
+    }
+    // bounded wait for the commit (the MMAs take well under a millisecond)
+    const long long w0 = clock64();
+    bool ok = false;
+    while (true) {
+        uint32_t r;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(r)
+            : "r"(smem_addr(&done)), "r"(0)
+            : "memory");
+        if (r) {
+            ok = true;
+            break;
+        }
+        if (clock64() - w0 > (1LL << 31)) break;
+    }
+    if (!ok && tid == 0) atomicOr(err, 1ULL);
+    if (blockIdx.x == 0 && tid == 0) *cycles = clock64() - t0;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    // the issue loop takes a few million cycles, so after a wait of 2^31 cycles no MMA is in
+    // flight whatever the outcome: the tensor memory is always freed
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kMmaN));
+    }
+}
+
 template <int KIND>
 static cudaError_t run(int grid, int iters, cudaStream_t st, float* sink, long long* cyc, float* ms)
 {
@@ -108,9 +202,61 @@ static cudaError_t run(int grid, int iters, cudaStream_t st, float* sink, long l
 
 using namespace mp3;
 
+// kinds 3 (BF16) and 4 (TF32): two CTAs per SM, each with its own accumulator; best of three
+// timed launches after one warm-up
+static mp3pcf_status mma_peak(bool tf32, cudaStream_t st, double* flops, double* mhz)
+{
+    int dev = 0, n_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return MP3PCF_ECUDA;
+    const int grid = 2 * n_sm, iters = 16384;
+    unsigned long long* err = nullptr;
+    long long* cyc = nullptr;
+    if (cudaMalloc(&err, sizeof(unsigned long long)) != cudaSuccess) return MP3PCF_ENOMEM;
+    if (cudaMalloc(&cyc, sizeof(long long)) != cudaSuccess) {
+        cudaFree(err);
+        return MP3PCF_ENOMEM;
+    }
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(unsigned long long), st);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, st);
+        if (tf32)
+            peaks::mma_probe_kernel<true><<<grid, 128, 0, st>>>(iters, err, cyc);
+        else
+            peaks::mma_probe_kernel<false><<<grid, 128, 0, st>>>(iters, err, cyc);
+        cudaEventRecord(e1, st);
+        e = cudaEventSynchronize(e1);
+        float t = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e == cudaSuccess && rep > 0) best = std::min(best, t);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    unsigned long long herr = 0;
+    long long hcyc = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&hcyc, cyc, sizeof(hcyc), cudaMemcpyDeviceToHost);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(err);
+    cudaFree(cyc);
+    if (e != cudaSuccess) return MP3PCF_ECUDA;
+    if (herr) return MP3PCF_ETIMEOUT;
+    const double k = tf32 ? 8.0 : 16.0;
+    *flops = 2.0 * peaks::kMmaM * peaks::kMmaN * k * iters * grid / (best * 1e-3);
+    // one CTA's cycles over its share of the launch (the two CTAs of an SM share its tensor core)
+    if (mhz) *mhz = (double)hcyc / (best * 1e3);
+    return MP3PCF_OK;
+}
+
 extern "C" mp3pcf_status mp3pcf_measure_peak(int32_t kind, void* stream, double* h_flops_per_s, double* h_sm_mhz)
 {
-    if (kind < 0 || kind > 2 || !h_flops_per_s) return MP3PCF_EINVAL;
+    if (kind < 0 || kind > 4 || !h_flops_per_s) return MP3PCF_EINVAL;
+    if (kind >= 3) return mma_peak(kind == 4, (cudaStream_t)stream, h_flops_per_s, h_sm_mhz);
     int dev = 0, n_sm = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)

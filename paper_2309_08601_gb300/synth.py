@@ -220,6 +220,10 @@ WORKLOADS = {
     "multiscale_310k": dict(n=310_000, side=190.0, field="lognormal", weights="uniform", seed=5,
                             sigma_e=0.0, n_bins=33, theta_min=0.25, theta_max=80.0, n_max=30,
                             grid_base_arcmin=0.25),
+    # the same at the paper's full area (3.1e6 galaxies on 100 deg^2)
+    "multiscale_3m": dict(n=3_100_000, side=600.0, field="lognormal", weights="uniform", seed=6,
+                          sigma_e=0.0, n_bins=33, theta_min=0.25, theta_max=80.0, n_max=30,
+                          grid_base_arcmin=0.25, theta_ap=[2.0, 4.0, 8.0, 16.0]),
 }
 
 
