@@ -339,7 +339,8 @@ def measure_combined(api, precision: str, stream, name: str = "multiscale_310k")
     cset = dict(n_bins=p["n_bins"], theta_min=p["theta_min"], theta_max=p["theta_max"], n_max=p["n_max"])
     with api.Estimator(**cset, precision=precision, stream=stream) as ec:
         edges = ec.bin_edges()[0]
-        levels = synth.grid_levels(edges, int(round(p["grid_base_arcmin"] / synth.QUANTUM)), synth.QUANTUM)
+        levels = synth.grid_levels(edges, int(round(p["grid_base_arcmin"] / synth.QUANTUM)), synth.QUANTUM,
+                                   max_q=int(round(p["grid_max_arcmin"] / synth.QUANTUM)))
 
         def run(combined):
             if combined:
@@ -367,6 +368,9 @@ def measure_combined(api, precision: str, stream, name: str = "multiscale_310k")
     ud, nd, uc, nc = out[False][2], out[False][3], out[True][2], out[True][3]
     gd, gcm = out[False][4], out[True][4]
     eq = [float(np.abs(gcm[b, b] - gd[b, b]).max() / np.abs(gd[b, b]).max()) for b in range(b0, nb)]
+    # equilateral triangles proper: theta_1 = theta_2 and phi = 60 deg (the two angular nodes around it)
+    k60 = [int(np.floor(gd.shape[-1] / 6.0 - 0.5)), int(np.ceil(gd.shape[-1] / 6.0 - 0.5))]
+    eq60 = [float(np.abs(gcm[b, b, k60] - gd[b, b, k60]).max() / np.abs(gd[b, b, k60]).max()) for b in range(b0, nb)]
 
     def nerr(a, b):
         return float(np.linalg.norm(a - b) / np.linalg.norm(b))
@@ -379,8 +383,10 @@ def measure_combined(api, precision: str, stream, name: str = "multiscale_310k")
             "grid_blocks_rel_err_upsilon_n_le_10": nerr(uc[:, :, :11][..., grid], ud[:, :, :11][..., grid]),
             "grid_blocks_rel_err_norm_n_le_20": nerr(nc[:, :21][..., grid], nd[:, :21][..., grid]),
             "grid_blocks_rel_err_upsilon_n_le_3": nerr(uc[:, :, :4][..., grid], ud[:, :, :4][..., grid]),
-            "equilateral_gamma0_rel_err_median": float(np.median(eq)),
-            "equilateral_gamma0_rel_err_max": float(np.max(eq)),
+            "equal_sides_gamma0_rel_err_over_phi_median": float(np.median(eq)),
+            "equal_sides_gamma0_rel_err_over_phi_max": float(np.max(eq)),
+            "equilateral_gamma0_rel_err_median": float(np.median(eq60)),
+            "equilateral_gamma0_rel_err_max": float(np.max(eq60)),
             "discrete_block_rel_err": float(np.abs(uc[..., ~grid] - ud[..., ~grid]).max() /
                                             np.abs(ud[..., ~grid]).max())}
 

@@ -219,26 +219,27 @@ WORKLOADS = {
     # 100 deg^2, 33 logarithmic bins 0.25'-80', noise-free) on a tenth of the area
     "multiscale_310k": dict(n=310_000, side=190.0, field="lognormal", weights="uniform", seed=5,
                             sigma_e=0.0, n_bins=33, theta_min=0.25, theta_max=80.0, n_max=30,
-                            grid_base_arcmin=0.25),
+                            grid_base_arcmin=0.25, grid_max_arcmin=1.0),
     # the same at the paper's full area (3.1e6 galaxies on 100 deg^2)
     "multiscale_3m": dict(n=3_100_000, side=600.0, field="lognormal", weights="uniform", seed=6,
                           sigma_e=0.0, n_bins=33, theta_min=0.25, theta_max=80.0, n_max=30,
-                          grid_base_arcmin=0.25, theta_ap=[2.0, 4.0, 8.0, 16.0]),
+                          grid_base_arcmin=0.25, grid_max_arcmin=1.0),
 }
 
 
-def grid_levels(edges, base_q: int, quantum: float, ratio: float = 20.0):
+def grid_levels(edges, base_q: int, quantum: float, ratio: float = 20.0, max_q: Optional[int] = None):
     """The combined estimator's levels (b_start, pixel_q) for bin edges (arcmin), as in the
     paper's accuracy test of it (ratio 20): pixels of side Delta (base_q quanta first) for the
-    bins with ratio Delta <= lower edge < 2 ratio Delta, then 2 Delta, and so on; the bins below
-    ratio base_q stay discrete."""
+    bins with ratio Delta <= lower edge < 2 ratio Delta, then 2 Delta, and so on, up to pixels of
+    max_q quanta (that test stops at 1'; None: no limit); the bins below ratio base_q stay
+    discrete."""
     levels = []
     d = int(base_q)
     for b in range(len(edges) - 1):
         lo = float(edges[b]) / quantum
         if lo < ratio * base_q:
             continue
-        while lo >= 2 * ratio * d:
+        while lo >= 2 * ratio * d and (max_q is None or 2 * d <= max_q):
             d *= 2
         if not levels or levels[-1][1] != d:
             levels.append((b, d))
