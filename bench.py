@@ -375,8 +375,9 @@ def measure_combined(api, precision: str, stream, name: str = "multiscale_310k")
     def nerr(a, b):
         return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
-    return {"workload": "multiscale_310k: %d galaxies on %g' (noise-free lognormal), %d bins %g'-%g', n_max %d"
-                        % (cat.n, p["side"], nb, p["theta_min"], p["theta_max"], p["n_max"]),
+    return {"workload": "%s: %d galaxies on %g' (noise-free lognormal, P(k) ~ k^%g), %d bins %g'-%g', n_max %d"
+                        % (name, cat.n, p["side"], p.get("slope", -1.5), nb, p["theta_min"], p["theta_max"],
+                           p["n_max"]),
             "levels": [[int(b), float(q * synth.QUANTUM)] for b, q in levels],
             "discrete_ms": out[False][0], "combined_ms": out[True][0], "speedup": out[False][0] / out[True][0],
             "discrete_pairs": int(out[False][1]), "combined_pairs": int(out[True][1]),
@@ -815,6 +816,7 @@ def run_gpu(args):
         line["combined"] = measure_combined(api, args.precision, stream)
     if rank == 0 and args.combined_full_area:
         line["combined_full_area"] = measure_combined(api, args.precision, stream, "multiscale_3m")
+        line["combined_full_area_smooth"] = measure_combined(api, args.precision, stream, "multiscale_3m_smooth")
 
     if rank == 0 and args.cpu_baseline:
         import oracle

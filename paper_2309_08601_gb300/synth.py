@@ -142,9 +142,10 @@ def uniform_positions(n: int, side: float, rng: np.random.Generator, holes=None)
 
 def make_catalog(n: int, side: float, seed: int, *, field: str = "noise", sigma_e: float = 0.26,
                  weights: str = "unit", ngrid: int = 4096, holes: bool = False,
-                 amplitude: float = 1.0, quantum: float = QUANTUM) -> Catalog:
+                 amplitude: float = 1.0, quantum: float = QUANTUM, slope: float = -1.5) -> Catalog:
     """One catalog. ``field`` is "noise" (pure shape noise) or "lognormal" (lognormal
-    Kaiser--Squires shear + noise); ``weights`` is "unit" or "uniform" (U(0.5, 1.5))."""
+    Kaiser--Squires shear + noise, the Gaussian field's P(k) ~ k^slope); ``weights`` is "unit" or
+    "uniform" (U(0.5, 1.5))."""
     rng = np.random.default_rng(seed)
     hl = hole_mask(side, rng) if holes else None
     x, y = uniform_positions(n, side, rng, hl)
@@ -152,7 +153,7 @@ def make_catalog(n: int, side: float, seed: int, *, field: str = "noise", sigma_
     g2 = np.zeros(n)
     meta = {"field": field, "seed": seed}
     if field == "lognormal":
-        _, s1, s2 = lognormal_shear_grid(ngrid, rng)
+        _, s1, s2 = lognormal_shear_grid(ngrid, rng, slope=slope)
         g1 += amplitude * _sample_grid(s1, x, y, side)
         g2 += amplitude * _sample_grid(s2, x, y, side)
         meta["ngrid"] = ngrid
@@ -224,6 +225,10 @@ WORKLOADS = {
     "multiscale_3m": dict(n=3_100_000, side=600.0, field="lognormal", weights="uniform", seed=6,
                           sigma_e=0.0, n_bins=33, theta_min=0.25, theta_max=80.0, n_max=30,
                           grid_base_arcmin=0.25, grid_max_arcmin=1.0),
+    # the same with a redder Gaussian field (P(k) ~ k^-3: less power at the pixel scales)
+    "multiscale_3m_smooth": dict(n=3_100_000, side=600.0, field="lognormal", weights="uniform", seed=6,
+                                 sigma_e=0.0, n_bins=33, theta_min=0.25, theta_max=80.0, n_max=30,
+                                 grid_base_arcmin=0.25, grid_max_arcmin=1.0, slope=-3.0),
 }
 
 
@@ -250,4 +255,4 @@ def workload_catalog(name: str, ngrid: int = 4096, n: Optional[int] = None) -> C
     p = WORKLOADS[name]
     return make_catalog(n if n is not None else p["n"], p["side"], p["seed"], field=p["field"],
                         weights=p["weights"], ngrid=ngrid, holes=p.get("holes", False),
-                        sigma_e=p.get("sigma_e", 0.26))
+                        sigma_e=p.get("sigma_e", 0.26), slope=p.get("slope", -1.5))
