@@ -327,69 +327,78 @@ def measure_combined(api, precision: str, stream, name: str = "multiscale_310k")
     """The combined estimator (Sec. 3.3) against the discrete one on a noise-free multi-scale
     workload (the density and binning of the paper's accuracy test of it: multiscale_310k on a
     tenth of its area, multiscale_3m on all of it): moments and contraction of each, timed with
-    CUDA events after one untimed run; the levels start at 20 pixels of 0.25' and double the pixel
-    every octave, as in that test. Differences: the multipoles norm-wise over every block with a
-    grid bin, and the centroid-projected Gamma_0 on the equilateral grid bins, per bin the largest
-    difference over phi relative to the largest |Gamma_0| (the measure of the paper's figure)."""
+    CUDA events after one untimed run, with the grid levels by direct pixel-pair sums and by FFT
+    convolution (grid_fft); the levels start at 20 pixels of 0.25' and double the pixel every
+    octave up to 1', as in that test. Differences against the discrete estimator: the multipoles
+    norm-wise over every block with a grid bin, and the centroid-projected Gamma_0 of the
+    equal-side bins (largest difference over phi, and at phi = 60 deg, relative to the largest
+    |Gamma_0|: the measure of the paper's figure)."""
     import torch
     from paper_2309_08601_gb300 import synth
     p = synth.WORKLOADS[name]
     cat = synth.workload_catalog(name)
     dev = api.catalog_to_device(cat)
     cset = dict(n_bins=p["n_bins"], theta_min=p["theta_min"], theta_max=p["theta_max"], n_max=p["n_max"])
-    with api.Estimator(**cset, precision=precision, stream=stream) as ec:
-        edges = ec.bin_edges()[0]
-        levels = synth.grid_levels(edges, int(round(p["grid_base_arcmin"] / synth.QUANTUM)), synth.QUANTUM,
-                                   max_q=int(round(p["grid_max_arcmin"] / synth.QUANTUM)))
+    out = {}
+    levels = None
+    for mode in ("discrete", "direct", "fft"):
+        with api.Estimator(**cset, precision=precision, stream=stream, grid_fft=(mode == "fft")) as ec:
+            if levels is None:
+                edges = ec.bin_edges()[0]
+                levels = synth.grid_levels(edges, int(round(p["grid_base_arcmin"] / synth.QUANTUM)), synth.QUANTUM,
+                                           max_q=int(round(p["grid_max_arcmin"] / synth.QUANTUM)))
 
-        def run(combined):
-            if combined:
-                ec.accumulate_moments_combined(*dev[:5], levels=levels)
-            else:
-                ec.accumulate_moments(*dev[:5])
-            return ec.contract()
+            def run():
+                if mode == "discrete":
+                    ec.accumulate_moments(*dev[:5])
+                else:
+                    ec.accumulate_moments_combined(*dev[:5], levels=levels)
+                return ec.contract()
 
-        out = {}
-        for combined in (False, True):
-            run(combined)
+            run()
             torch.cuda.synchronize()
             t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             t0.record(stream)
-            ups, norm = run(combined)
+            ups, norm = run()
             t1.record(stream)
             torch.cuda.synchronize()
             gam, _ = ec.edge_correct(ups, norm, report_singular=False)
             g0 = ec.to_gamma(gam, 1)[0, 0].cpu().numpy()
-            out[combined] = (t0.elapsed_time(t1), ec.counts()[1], ups.cpu().numpy(), norm.cpu().numpy(), g0)
+            out[mode] = (t0.elapsed_time(t1), ec.counts()[1], ups.cpu().numpy(), norm.cpu().numpy(), g0)
     b0 = levels[0][0]
     nb = p["n_bins"]
     grid = np.zeros((nb, nb), bool)
     grid[b0:, :] = grid[:, b0:] = True
-    ud, nd, uc, nc = out[False][2], out[False][3], out[True][2], out[True][3]
-    gd, gcm = out[False][4], out[True][4]
-    eq = [float(np.abs(gcm[b, b] - gd[b, b]).max() / np.abs(gd[b, b]).max()) for b in range(b0, nb)]
-    # equilateral triangles proper: theta_1 = theta_2 and phi = 60 deg (the two angular nodes around it)
+    ud, nd, gd = out["discrete"][2], out["discrete"][3], out["discrete"][4]
     k60 = [int(np.floor(gd.shape[-1] / 6.0 - 0.5)), int(np.ceil(gd.shape[-1] / 6.0 - 0.5))]
-    eq60 = [float(np.abs(gcm[b, b, k60] - gd[b, b, k60]).max() / np.abs(gd[b, b, k60]).max()) for b in range(b0, nb)]
 
     def nerr(a, b):
         return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
-    return {"workload": "%s: %d galaxies on %g' (noise-free lognormal, P(k) ~ k^%g), %d bins %g'-%g', n_max %d"
-                        % (name, cat.n, p["side"], p.get("slope", -1.5), nb, p["theta_min"], p["theta_max"],
-                           p["n_max"]),
-            "levels": [[int(b), float(q * synth.QUANTUM)] for b, q in levels],
-            "discrete_ms": out[False][0], "combined_ms": out[True][0], "speedup": out[False][0] / out[True][0],
-            "discrete_pairs": int(out[False][1]), "combined_pairs": int(out[True][1]),
-            "grid_blocks_rel_err_upsilon_n_le_10": nerr(uc[:, :, :11][..., grid], ud[:, :, :11][..., grid]),
-            "grid_blocks_rel_err_norm_n_le_20": nerr(nc[:, :21][..., grid], nd[:, :21][..., grid]),
-            "grid_blocks_rel_err_upsilon_n_le_3": nerr(uc[:, :, :4][..., grid], ud[:, :, :4][..., grid]),
-            "equal_sides_gamma0_rel_err_over_phi_median": float(np.median(eq)),
-            "equal_sides_gamma0_rel_err_over_phi_max": float(np.max(eq)),
-            "equilateral_gamma0_rel_err_median": float(np.median(eq60)),
-            "equilateral_gamma0_rel_err_max": float(np.max(eq60)),
-            "discrete_block_rel_err": float(np.abs(uc[..., ~grid] - ud[..., ~grid]).max() /
-                                            np.abs(ud[..., ~grid]).max())}
+    res = {"workload": "%s: %d galaxies on %g' (noise-free lognormal, P(k) ~ k^%g), %d bins %g'-%g', n_max %d"
+                       % (name, cat.n, p["side"], p.get("slope", -1.5), nb, p["theta_min"], p["theta_max"],
+                          p["n_max"]),
+           "levels": [[int(b), float(q * synth.QUANTUM)] for b, q in levels],
+           "discrete_ms": out["discrete"][0], "discrete_pairs": int(out["discrete"][1])}
+    for mode in ("direct", "fft"):
+        uc, nc, gcm = out[mode][2], out[mode][3], out[mode][4]
+        eq = [float(np.abs(gcm[b, b] - gd[b, b]).max() / np.abs(gd[b, b]).max()) for b in range(b0, nb)]
+        eq60 = [float(np.abs(gcm[b, b, k60] - gd[b, b, k60]).max() / np.abs(gd[b, b, k60]).max())
+                for b in range(b0, nb)]
+        res[mode] = {"ms": out[mode][0], "speedup": out["discrete"][0] / out[mode][0],
+                     "pairs_counted": int(out[mode][1]),
+                     "grid_blocks_rel_err_upsilon_n_le_3": nerr(uc[:, :, :4][..., grid], ud[:, :, :4][..., grid]),
+                     "grid_blocks_rel_err_upsilon_n_le_10": nerr(uc[:, :, :11][..., grid], ud[:, :, :11][..., grid]),
+                     "grid_blocks_rel_err_norm_n_le_20": nerr(nc[:, :21][..., grid], nd[:, :21][..., grid]),
+                     "equal_sides_gamma0_rel_err_over_phi_median": float(np.median(eq)),
+                     "equal_sides_gamma0_rel_err_over_phi_max": float(np.max(eq)),
+                     "equilateral_gamma0_rel_err_median": float(np.median(eq60)),
+                     "equilateral_gamma0_rel_err_max": float(np.max(eq60)),
+                     "discrete_block_rel_err": float(np.abs(uc[..., ~grid] - ud[..., ~grid]).max() /
+                                                     np.abs(ud[..., ~grid]).max())}
+    res["fft_vs_direct_upsilon_rel_err"] = nerr(out["fft"][2], out["direct"][2])
+    res["fft_vs_direct_norm_rel_err"] = nerr(out["fft"][3], out["direct"][3])
+    return res
 
 
 def cpu_model() -> str:

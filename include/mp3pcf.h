@@ -64,7 +64,11 @@ typedef struct {
     int32_t exclude_degenerate; /* 1: leave the triplets with j = k (one neighbour in both legs, so
                                  * b1 = b2 and Z2 = Z3) out of Upsilon and N; 0 (default): the
                                  * paper's sums over all (i, j, k) */
-    int32_t reserved[2];     /* must be zero */
+    int32_t grid_fft;        /* combined estimator (mp3pcf_accumulate_moments_combined): 1 evaluates
+                              * the grid levels' moments by FFT convolution of the gridded fields with
+                              * the bin kernels (Sec. 3.2), 0 (default) by direct sums over pixel pairs;
+                              * the two agree to the FFT's rounding */
+    int32_t reserved;        /* must be zero */
 } mp3pcf_config;
 
 typedef struct mp3pcf_ctx mp3pcf_ctx;

@@ -59,11 +59,11 @@ class Estimator:
     def __init__(self, n_bins, theta_min, theta_max, n_max, *, n_phi=100, n_z=1,
                  quantum=2.0 ** -13, precision="fp32", norm_truncate=False,
                  radial_nodes="arithmetic", cell_occupancy=0, contract_slices=0,
-                 exclude_degenerate=False, stream=None):
+                 exclude_degenerate=False, grid_fft=False, stream=None):
         torch = _torch()
         self.cfg = native.make_config(n_bins, theta_min, theta_max, n_max, n_phi, n_z, quantum,
                                       precision, norm_truncate, radial_nodes, cell_occupancy,
-                                      contract_slices, exclude_degenerate)
+                                      contract_slices, exclude_degenerate, grid_fft)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.precision = precision

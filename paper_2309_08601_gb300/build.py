@@ -69,7 +69,7 @@ def build_native(force: bool = False, verbose: bool = False, extra_flags=()) -> 
             list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp%d" % os.getpid()
-        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcufft"])
         os.replace(tmp, LIB)
     return LIB
 

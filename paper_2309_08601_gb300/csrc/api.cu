@@ -376,6 +376,8 @@ struct mp3pcf_ctx {
     DevBuf degen;                       // exclude_degenerate sums per (centre, z, bin)
     DevBuf degen_grad;                  // their gradient sums per (Z1, z, bin) in the adjoint
     DevBuf zrange;                      // [nz + 1] centre range of each z-bin
+    DevBuf fftwork;                     // FFT grid moments: padded fields, kernels, products
+    FftPlanCache* fft = nullptr;        // cuFFT plans of the FFT grid moments
     DevBuf gridsum;                     // per-pixel FP64 sums of the grid-based approximation
     DevBuf gridflag;                    // its non-empty flags and their exclusive scan
     // combined estimator: the moments of the last accumulate call mix discrete and grid bins
@@ -476,8 +478,8 @@ static bool config_valid(const mp3pcf_config* c, std::string* why)
     if (c->cell_occupancy < 0 || c->cell_occupancy > 64) return bad("cell_occupancy out of range");
     if (c->contract_slices < 0 || c->contract_slices > 64) return bad("contract_slices out of range");
     if (c->exclude_degenerate != 0 && c->exclude_degenerate != 1) return bad("exclude_degenerate");
-    for (int r : c->reserved)
-        if (r != 0) return bad("reserved fields must be zero");
+    if (c->grid_fft != 0 && c->grid_fft != 1) return bad("grid_fft");
+    if (c->reserved != 0) return bad("reserved fields must be zero");
     const double t = c->theta_max / c->quantum;
     if (t * t >= 9.0e18) return bad("theta_max / quantum too large");
     return true;
@@ -560,10 +562,11 @@ mp3pcf_status mp3pcf_destroy(mp3pcf_ctx* ctx)
                       &ctx->pos, &ctx->pay, &ctx->zs, &ctx->cflag,
                       &ctx->crank, &ctx->oflag, &ctx->orank, &ctx->centre_idx, &ctx->crow,
                       &ctx->G, &ctx->W, &ctx->pairs, &ctx->partial, &ctx->singular,
-                      &ctx->m3partial, &ctx->m3four, &ctx->ccoef, &ctx->gG, &ctx->gW, &ctx->gv, &ctx->gtab,
+                      &ctx->m3partial, &ctx->m3four, &ctx->fftwork, &ctx->ccoef, &ctx->gG, &ctx->gW, &ctx->gv, &ctx->gtab,
                       &ctx->adjscratch, &ctx->degen, &ctx->degen_grad, &ctx->zrange, &ctx->gridsum, &ctx->gridflag, &ctx->bups, &ctx->bnorm,
                       &ctx->bgam, &ctx->bgcen, &ctx->berr, &ctx->pix, &ctx->pixinv};
     for (DevBuf* b : bufs) b->release();
+    if (ctx->fft) fft_cache_destroy(ctx->fft);
     if (ctx->sub) mp3pcf_destroy(ctx->sub);
     if (ctx->batch_st) cudaStreamDestroy(ctx->batch_st);
     for (cudaEvent_t ev : ctx->batch_ev)
@@ -832,6 +835,25 @@ static mp3pcf_status combined_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq, c
         ctx->launches[ST_MOMENTS] += 8;
         MP3_CK(launch_grid_sums(n, xq, yq, g1, g2, w, zb, nz, x0, y0, pq, (int)npx, (int)npy,
                                 ctx->gridsum.as<double>(), flags, ctx->n_sm, ctx->st));
+        if (c.grid_fft) {
+            // the level's moments by FFT convolution of the gridded fields (no pixel catalog)
+            if (!ctx->fft) ctx->fft = fft_cache_create();
+            std::vector<long long> e2q(nb + 1);
+            if (mp3pcf_bin_edges(&c, nullptr, reinterpret_cast<int64_t*>(e2q.data())) != MP3PCF_OK)
+                return fail(ctx, MP3PCF_EINVAL, "bin edges");
+            const size_t wb = grid_fft_work_bytes(nz, b1 - b0, (int)npx, (int)npy,
+                                                  std::sqrt((double)e2q[b1]) / (double)pq, sizeof(T),
+                                                  std::max(2 * c.n_max, c.n_max + 3) + 1, (size_t)6 << 30);
+            MP3_CK(ctx->fftwork.ensure(wb));
+            ctx->launches[ST_MOMENTS] += 2;
+            const char* what = "";
+            const cudaError_t fe = grid_fft_moments<T>(
+                ctx->fft, nc, nz, nb, b0, b1, c.n_max, e2q.data(), ctx->centre_idx.as<int>(), ctx->pos.as<int2>(), czs,
+                x0, y0, pq, (int)npx, (int)npy, ctx->gridsum.as<double>(), ctx->fftwork.p, wb, ctx->G.as<cx<T>>(),
+                ctx->W.as<cx<T>>(), ctx->n_sm, ctx->st, &what);
+            if (fe != cudaSuccess) return fail(ctx, MP3PCF_ECUDA, (std::string("FFT grid moments: ") + what).c_str());
+            continue;
+        }
         if (mp3pcf_status s = scan_exclusive(ctx, flags, rank, npix)) return s;
         MP3_CK(launch_grid_emit(nz, (int)npx, (int)npy, x0, y0, pq, ctx->gridsum.as<double>(), rank, pxq, pyq, pg1,
                                 pg2, pw, nz > 1 ? pzb : nullptr, ctx->n_sm, ctx->st));

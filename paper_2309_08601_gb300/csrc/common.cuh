@@ -165,6 +165,20 @@ cudaError_t launch_grid_gather(int64_t nc, int nz, int nb, int b0, int b1, int n
                                const int* sub_perm, int* inv, int* srow, const cx<T>* Gs, const cx<T>* Ws, cx<T>* G,
                                cx<T>* W, const unsigned long long* sub_pairs, unsigned long long* pairs, int n_sm,
                                cudaStream_t st);
+// combined estimator, FFT form of a grid level (csrc/grid_fft.cu): the moments of bins [b0, b1) of
+// every centre from the level's pixel sums (gridsum [nz][npy][npx][3], FP64) by FFT convolution
+// with the bin kernels; work holds work_bytes of device scratch (grid_fft_work_bytes)
+struct FftPlanCache;
+FftPlanCache* fft_cache_create();
+void fft_cache_destroy(FftPlanCache* c);
+size_t grid_fft_work_bytes(int nz, int nbr, int npx, int npy, double rmax_pixels, size_t elem_bytes, int max_orders,
+                           size_t budget);
+template <typename T>
+cudaError_t grid_fft_moments(FftPlanCache* cache, int64_t nc, int nz, int nb, int b0, int b1, int n_max,
+                             const long long* h_e2q, const int* centre_idx, const int2* pos, const uint8_t* zs,
+                             long long x0, long long y0, long long pq, int npx, int npy, const double* gridsum,
+                             void* work, size_t work_bytes, cx<T>* G, cx<T>* W, int n_sm, cudaStream_t st,
+                             const char** what);
 // direct estimator of <M_ap^3> (Sec. 5.3): out[centre][radii triple][2] = (numerator, denominator)
 cudaError_t launch_map3_direct(int64_t n, const int32_t* xq, const int32_t* yq, const float* g1, const float* g2,
                                const float* w, double quantum, int64_t n_cen, const double* centres, int n_ap,

@@ -23,7 +23,7 @@ class Config(C.Structure):
                 ("quantum", C.c_double), ("precision", C.c_int32), ("norm_truncate", C.c_int32),
                 ("radial_nodes", C.c_int32), ("cell_occupancy", C.c_int32),
                 ("contract_slices", C.c_int32), ("exclude_degenerate", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("grid_fft", C.c_int32), ("reserved", C.c_int32)]
 
 
 P = C.c_void_p
@@ -107,10 +107,10 @@ def check(status: int, where: str, ctx=None, ok=(OK,)):
 
 def make_config(n_bins, theta_min, theta_max, n_max, n_phi=100, n_z=1, quantum=2.0 ** -13,
                 precision="fp32", norm_truncate=False, radial_nodes="arithmetic", cell_occupancy=0,
-                contract_slices=0, exclude_degenerate=False) -> Config:
+                contract_slices=0, exclude_degenerate=False, grid_fft=False) -> Config:
     return Config(int(n_bins), float(theta_min), float(theta_max), int(n_max), int(n_phi), int(n_z),
                   float(quantum), PRECISIONS[precision] if isinstance(precision, str) else int(precision),
                   int(bool(norm_truncate)),
                   {"arithmetic": 0, "geometric": 1}[radial_nodes] if isinstance(radial_nodes, str)
                   else int(radial_nodes), int(cell_occupancy), int(contract_slices),
-                  int(bool(exclude_degenerate)), (C.c_int32 * 2)())
+                  int(bool(exclude_degenerate)), int(bool(grid_fft)), 0)

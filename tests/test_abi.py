@@ -62,13 +62,14 @@ def test_bad_configurations_are_rejected_before_any_cuda_call(lib, field, value)
 
 def test_reserved_fields_must_be_zero(lib):
     cfg = lib.make_config(10, 0.5, 30.0, 10)
-    cfg.reserved[1] = 1
+    cfg.reserved = 1
     ctx = C.c_void_p()
     assert lib.lib().mp3pcf_create(C.byref(cfg), None, C.byref(ctx)) == lib.EINVAL
 
 
 @pytest.mark.parametrize("field,value", [("cell_occupancy", 65), ("cell_occupancy", -1),
-                                         ("contract_slices", 65), ("exclude_degenerate", 2)])
+                                         ("contract_slices", 65), ("exclude_degenerate", 2),
+                                         ("grid_fft", 2)])
 def test_tuning_and_variant_fields_are_validated(lib, field, value):
     cfg = lib.make_config(10, 0.5, 30.0, 10)
     setattr(cfg, field, value)

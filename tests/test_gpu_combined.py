@@ -36,10 +36,13 @@ def _catalog(n_z):
     return cat
 
 
+@pytest.mark.parametrize("grid_fft", [False, True])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-4), ("bf16x3", 1e-4)])
 @pytest.mark.parametrize("n_z", [1, 2])
 @pytest.mark.parametrize("subset", [False, True])
-def test_combined_moments_and_multipoles_match_the_oracle(gpu, orc, precision, tol, n_z, subset):
+def test_combined_moments_and_multipoles_match_the_oracle(gpu, orc, precision, tol, n_z, subset, grid_fft):
+    """Direct pixel-pair sums and the FFT form (grid_fft) of the grid levels, each against the
+    oracle's combined moments (its pixel sums by direct loops) and their contraction."""
     cat = _catalog(n_z)
     rng = np.random.default_rng(7)
     mask = (rng.uniform(size=cat.n) < 0.4).astype(np.uint8) if subset else None
@@ -49,7 +52,7 @@ def test_combined_moments_and_multipoles_match_the_oracle(gpu, orc, precision, t
     u0, n0 = orc.contract(s, cat, G0, W0, centres)
     dev = gpu.catalog_to_device(cat)
     m = None if mask is None else torch.as_tensor(mask, device=dev[0].device)
-    with gpu.Estimator(**SETUP, n_z=n_z, precision=precision) as est:
+    with gpu.Estimator(**SETUP, n_z=n_z, precision=precision, grid_fft=grid_fft) as est:
         est.accumulate_moments_combined(*dev[:5], dev[5], m, levels=LEVELS)
         nc, npairs = est.counts()
         assert nc == len(centres) and npairs > 0
@@ -60,6 +63,29 @@ def test_combined_moments_and_multipoles_match_the_oracle(gpu, orc, precision, t
     assert max(errs) < tol, errs
     # the grid bins of a galaxy alone in a weightless pixel are zero on both sides
     assert np.array_equal(G[:, :, 2:] == 0, G0[:, :, 2:] == 0)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_fft_grid_moments_equal_the_pixel_pair_sums(gpu, precision, tol):
+    """The FFT form of the grid levels against the direct pixel-pair sums on a denser field with
+    three levels and many pixels per bin: the same pixel fields, bin tests and angles, so they
+    differ by the FFT's rounding only (FP64 ~1e-13, FP32 ~1e-6 normwise)."""
+    cat = synth.make_catalog(40000, 60.0, 9, field="lognormal", weights="uniform", ngrid=1024)
+    setup = dict(n_bins=12, theta_min=0.5, theta_max=20.0, n_max=8)
+    edges = 0.5 * 40.0 ** (np.arange(13) / 12)
+    levels = synth.grid_levels(edges, 1 << 10, 2.0 ** -13, ratio=10.0)
+    assert len(levels) >= 3
+    dev = gpu.catalog_to_device(cat)
+    out = {}
+    for fft in (False, True):
+        with gpu.Estimator(**setup, precision=precision, grid_fft=fft) as est:
+            est.accumulate_moments_combined(*dev[:5], levels=levels)
+            G, W = est.moments()
+            ups, norm = est.contract()
+            out[fft] = (G.cpu().numpy(), W.cpu().numpy(), ups.cpu().numpy(), norm.cpu().numpy())
+    errs = [rel_err(a, b) for a, b in zip(out[True], out[False])]
+    print(precision, "FFT vs pixel pairs (G, W, Upsilon, N):", errs)
+    assert max(errs) < tol, errs
 
 
 def test_all_bins_on_the_grid_and_empty_catalogs(gpu, orc):
