@@ -822,7 +822,7 @@ def run_gpu(args):
 
     # ---- the combined estimator against the discrete one (rank 0)
     if rank == 0 and args.combined:
-        line["combined"] = measure_combined(api, args.precision, stream)
+        line["combined"] = measure_combined(api, args.precision, stream, args.combined_workload)
     if rank == 0 and args.combined_full_area:
         line["combined_full_area"] = measure_combined(api, args.precision, stream, "multiscale_3m")
         line["combined_full_area_smooth"] = measure_combined(api, args.precision, stream, "multiscale_3m_smooth")
@@ -879,6 +879,8 @@ def main(argv=None):
                     help="skip the combined-versus-discrete estimator timing")
     ap.add_argument("--combined-full-area", action="store_true",
                     help="also the combined-versus-discrete comparison at the paper's full area (3.1e6 galaxies)")
+    ap.add_argument("--combined-workload", default="multiscale_310k",
+                    help="workload of the default combined-estimator leg")
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     ap.add_argument("--oracle-plan", action="store_true",
                     help="with --impl reference: the oracle's timing plan over every workload")

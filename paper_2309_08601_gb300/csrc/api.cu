@@ -841,7 +841,7 @@ static mp3pcf_status combined_t(mp3pcf_ctx* ctx, int64_t n, const int32_t* xq, c
             std::vector<long long> e2q(nb + 1);
             if (mp3pcf_bin_edges(&c, nullptr, reinterpret_cast<int64_t*>(e2q.data())) != MP3PCF_OK)
                 return fail(ctx, MP3PCF_EINVAL, "bin edges");
-            const size_t wb = grid_fft_work_bytes(nz, b1 - b0, (int)npx, (int)npy,
+            const size_t wb = grid_fft_work_bytes(nc, nz, b1 - b0, (int)npx, (int)npy,
                                                   std::sqrt((double)e2q[b1]) / (double)pq, sizeof(T),
                                                   std::max(2 * c.n_max, c.n_max + 3) + 1, (size_t)6 << 30);
             MP3_CK(ctx->fftwork.ensure(wb));

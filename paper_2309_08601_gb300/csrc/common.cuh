@@ -171,8 +171,8 @@ cudaError_t launch_grid_gather(int64_t nc, int nz, int nb, int b0, int b1, int n
 struct FftPlanCache;
 FftPlanCache* fft_cache_create();
 void fft_cache_destroy(FftPlanCache* c);
-size_t grid_fft_work_bytes(int nz, int nbr, int npx, int npy, double rmax_pixels, size_t elem_bytes, int max_orders,
-                           size_t budget);
+size_t grid_fft_work_bytes(int64_t nc, int nz, int nbr, int npx, int npy, double rmax_pixels, size_t elem_bytes,
+                           int max_orders, size_t budget);
 template <typename T>
 cudaError_t grid_fft_moments(FftPlanCache* cache, int64_t nc, int nz, int nb, int b0, int b1, int n_max,
                              const long long* h_e2q, const int* centre_idx, const int2* pos, const uint8_t* zs,

@@ -36,14 +36,19 @@ struct FftPlanCache {
 FftPlanCache* fft_cache_create() { return new FftPlanCache(); }
 void fft_cache_destroy(FftPlanCache* c) { delete c; }
 
-// smallest length >= n whose prime factors are 2, 3 and 5 (fast cuFFT sizes)
+#ifndef MP3_FFT_MAX35
+#define MP3_FFT_MAX35 99  // largest power of 3 and of 5 allowed in a transform length
+#endif
+
+// smallest length >= n of the form 2^a 3^b 5^c (b, c <= MP3_FFT_MAX35): fast cuFFT sizes
 static int fft_len(int n)
 {
     for (int m = n;; ++m) {
-        int r = m;
-        for (int p : {2, 3, 5})
-            while (r % p == 0) r /= p;
-        if (r == 1) return m;
+        int r = m, e3 = 0, e5 = 0;
+        while (r % 2 == 0) r /= 2;
+        while (r % 3 == 0) r /= 3, ++e3;
+        while (r % 5 == 0) r /= 5, ++e5;
+        if (r == 1 && e3 <= MP3_FFT_MAX35 && e5 <= MP3_FFT_MAX35) return m;
     }
 }
 
@@ -158,22 +163,13 @@ __global__ void k_fft_mul(int NX, int NY, int n, bool flip, const cx<T>* __restr
     }
 }
 
-// moment rows of every centre: for the orders j0 .. j1 - 1 of a batch of nk, order slot
-// slot0 + dir j, neighbour z-bin z, bins b0 .. b0 + nbr - 1 (P [nbr][nk][NY][NX]): the convolution
-// at the centre's pixel (normalised), zero where that pixel has no weight (it is not in the pixel
-// catalog of the direct form). One thread per (order, centre) writes its run of bins.
-template <typename T>
-__global__ void k_fft_gather(int64_t nc, int nk, int j0, int j1, int nbr, const int* __restrict__ centre_idx,
-                             const int2* __restrict__ pos, const uint8_t* __restrict__ zs, long long x0, long long y0,
-                             long long pq, int npx, int npy, int NX, int NY, const double* __restrict__ s,
-                             const cx<T>* __restrict__ P, T scale, int slot0, int dir, size_t plane_rows, int nz,
-                             int z, int nbp, int b0, cx<T>* __restrict__ out)
+// each centre's pixel on the padded grid (iy NX + ix), or -1 when that pixel has no weight (it is
+// not in the pixel catalog of the direct form, whose grid bins are then zero)
+__global__ void k_fft_centre_pixels(int64_t nc, const int* __restrict__ centre_idx, const int2* __restrict__ pos,
+                                    const uint8_t* __restrict__ zs, long long x0, long long y0, long long pq, int npx,
+                                    int npy, int NX, const double* __restrict__ s, int* __restrict__ cpx)
 {
-    const int64_t total = (int64_t)(j1 - j0) * nc;
-    const int64_t grid_plane = (int64_t)NX * NY;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int j = j0 + (int)(t / nc);
-        const int64_t c = t - (int64_t)(j - j0) * nc;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
         const int i = centre_idx[c];
         const int2 p = pos[i];
         const long long dx = (long long)p.x - x0, dy = (long long)p.y - y0;
@@ -181,11 +177,28 @@ __global__ void k_fft_gather(int64_t nc, int nk, int j0, int j1, int nbr, const 
         const int iy = (int)min(max(dy < 0 ? -1LL : dy / pq, 0LL), (long long)npy - 1);
         const int zc = zs ? (int)zs[i] : 0;
         const bool has = s[3 * (((int64_t)zc * npy + iy) * npx + ix)] > 0.0;
+        cpx[c] = has ? iy * NX + ix : -1;
+    }
+}
+
+// moment rows of every centre: for the orders j0 .. j1 - 1 of a batch of nk, order slot
+// slot0 + dir j, neighbour z-bin z, bins b0 .. b0 + nbr - 1 (P [nbr][nk][NY][NX]): the convolution
+// at the centre's pixel (normalised), zero for the centres without one. One thread per (order,
+// centre) writes its run of bins.
+template <typename T>
+__global__ void k_fft_gather(int64_t nc, int nk, int j0, int j1, int nbr, const int* __restrict__ cpx, int64_t grid_plane,
+                             const cx<T>* __restrict__ P, T scale, int slot0, int dir, size_t plane_rows, int nz,
+                             int z, int nbp, int b0, cx<T>* __restrict__ out)
+{
+    const int64_t total = (int64_t)(j1 - j0) * nc;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int j = j0 + (int)(t / nc);
+        const int64_t c = t - (int64_t)(j - j0) * nc;
+        const int px = cpx[c];
         cx<T>* o = out + (size_t)(slot0 + dir * j) * plane_rows + ((size_t)c * nz + z) * nbp + b0;
-        const int64_t px = (int64_t)iy * NX + ix;
         for (int bb = 0; bb < nbr; ++bb) {
             cx<T> v{T(0), T(0)};
-            if (has) {
+            if (px >= 0) {
                 const cx<T> g = P[((int64_t)bb * nk + j) * grid_plane + px];
                 v = cx<T>{g.x * scale, g.y * scale};
             }
@@ -216,8 +229,9 @@ cudaError_t grid_fft_moments(FftPlanCache* cache, int64_t nc, int nz, int nb, in
     const size_t pbytes = sizeof(cx<T>) * (size_t)plane;
     const int nbp = nb_pad(nb);
     const size_t plane_rows = (size_t)nc * nz * nbp;
-    // work: the level's squared edges, fields [2 nz], kernel spectra [nbr][nk], products [nbr][nk]
-    const size_t head = 1024;  // the level's squared edges (<= kMaxBins + 1 values)
+    // work: the level's squared edges, the centres' pixels, fields [2 nz], kernel spectra
+    // [nbr][nk], products [nbr][nk]
+    const size_t head = 1024 + ((sizeof(int) * (size_t)nc + 255) / 256) * 256;
     const size_t field_bytes = 2 * (size_t)nz * pbytes;
     if (work_bytes < head + field_bytes + 2 * (size_t)nbr * pbytes) {
         *what = "FFT workspace too small";
@@ -226,6 +240,7 @@ cudaError_t grid_fft_moments(FftPlanCache* cache, int64_t nc, int nz, int nb, in
     const int mtop = 2 * n_max > n_max + 3 ? 2 * n_max : n_max + 3;  // orders |m| <= mtop are needed
     const int nk_max = (int)std::min<size_t>((size_t)mtop + 1, (work_bytes - head - field_bytes) / (2 * (size_t)nbr * pbytes));
     long long* e2q = reinterpret_cast<long long*>(work);
+    int* cpx = reinterpret_cast<int*>(static_cast<char*>(work) + 1024);
     cx<T>* F = reinterpret_cast<cx<T>*>(static_cast<char*>(work) + head);
     cx<T>* K = F + 2 * (int64_t)nz * plane;
     cx<T>* P = K + (int64_t)nbr * nk_max * plane;
@@ -234,6 +249,9 @@ cudaError_t grid_fft_moments(FftPlanCache* cache, int64_t nc, int nz, int nb, in
     if (e != cudaSuccess) return e;
 
     k_fft_fields<T><<<fft_blocks((int64_t)nz * plane, n_sm), 256, 0, st>>>(nz, npx, npy, NX, NY, gridsum, F);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_fft_centre_pixels<<<fft_blocks(nc, n_sm), 256, 0, st>>>(nc, centre_idx, pos, zs, x0, y0, pq, npx, npy, NX,
+                                                              gridsum, cpx);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     cufftHandle hf = get_plan<T>(cache, NY, NX, 2 * nz, st, &fr);
     if (fr != CUFFT_SUCCESS || FftType<T>::exec(hf, F, CUFFT_FORWARD) != CUFFT_SUCCESS) {
@@ -273,8 +291,7 @@ cudaError_t grid_fft_moments(FftPlanCache* cache, int64_t nc, int nz, int nb, in
                     return cudaErrorUnknown;
                 }
                 k_fft_gather<T><<<fft_blocks((int64_t)(jn - j0) * nc, n_sm), 256, 0, st>>>(
-                    nc, nk, j0, jn, nbr, centre_idx, pos, zs, x0, y0, pq, npx, npy, NX, NY, gridsum, P, scale,
-                    slot0, dir, plane_rows, nz, z, nbp, b0, out);
+                    nc, nk, j0, jn, nbr, cpx, plane, P, scale, slot0, dir, plane_rows, nz, z, nbp, b0, out);
                 if ((e = cudaGetLastError()) != cudaSuccess) return e;
             }
         }
@@ -284,14 +301,15 @@ cudaError_t grid_fft_moments(FftPlanCache* cache, int64_t nc, int nz, int nb, in
 
 // workspace for a level of nbr bins: the fields and the kernel and product arrays of at least one
 // order per bin; up to max_orders orders per batch as the budget allows
-size_t grid_fft_work_bytes(int nz, int nbr, int npx, int npy, double rmax_pixels, size_t elem_bytes, int max_orders,
-                           size_t budget)
+size_t grid_fft_work_bytes(int64_t nc, int nz, int nbr, int npx, int npy, double rmax_pixels, size_t elem_bytes,
+                           int max_orders, size_t budget)
 {
     const int R = (int)std::ceil(rmax_pixels) + 1;
     const size_t plane = (size_t)fft_len(npx + R + 1) * fft_len(npy + R + 1);
     const size_t pbytes = 2 * elem_bytes * plane;
-    const size_t need = 1024 + (2 * (size_t)nz + 2 * (size_t)nbr) * pbytes;
-    const size_t want = 1024 + (2 * (size_t)nz + 2 * (size_t)nbr * max_orders) * pbytes;
+    const size_t head = 1024 + ((sizeof(int) * (size_t)nc + 255) / 256) * 256;
+    const size_t need = head + (2 * (size_t)nz + 2 * (size_t)nbr) * pbytes;
+    const size_t want = head + (2 * (size_t)nz + 2 * (size_t)nbr * max_orders) * pbytes;
     return std::max(need, std::min(want, budget));
 }
 
