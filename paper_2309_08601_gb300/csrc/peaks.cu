@@ -211,6 +211,13 @@ static mp3pcf_status mma_peak(bool tf32, cudaStream_t st, double* flops, double*
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return MP3PCF_ECUDA;
     const int grid = 2 * n_sm, iters = 16384;
+    // 96 KB of (unused) dynamic shared memory per CTA keeps at most two CTAs on an SM, so the two
+    // 256-column tensor-memory allocations of an SM never wait for each other
+    const size_t pad_smem = 96 * 1024;
+    cudaError_t ea = cudaFuncSetAttribute(peaks::mma_probe_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pad_smem);
+    if (ea == cudaSuccess)
+        ea = cudaFuncSetAttribute(peaks::mma_probe_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pad_smem);
+    if (ea != cudaSuccess) return MP3PCF_ECUDA;
     unsigned long long* err = nullptr;
     long long* cyc = nullptr;
     if (cudaMalloc(&err, sizeof(unsigned long long)) != cudaSuccess) return MP3PCF_ENOMEM;
@@ -226,9 +233,9 @@ static mp3pcf_status mma_peak(bool tf32, cudaStream_t st, double* flops, double*
     for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
         cudaEventRecord(e0, st);
         if (tf32)
-            peaks::mma_probe_kernel<true><<<grid, 128, 0, st>>>(iters, err, cyc);
+            peaks::mma_probe_kernel<true><<<grid, 128, pad_smem, st>>>(iters, err, cyc);
         else
-            peaks::mma_probe_kernel<false><<<grid, 128, 0, st>>>(iters, err, cyc);
+            peaks::mma_probe_kernel<false><<<grid, 128, pad_smem, st>>>(iters, err, cyc);
         cudaEventRecord(e1, st);
         e = cudaEventSynchronize(e1);
         float t = 0.0f;
