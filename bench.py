@@ -58,7 +58,9 @@ TRAFFIC_BYTES = {
     # moments_kernel<float,40>: capture at 100 000 galaxies of the same density, x10
     # (profiles/moments_kernel_masked_lognormal_100k.md)
     ("moments", "masked_lognormal_1m"): 10 * (630.813440e6 + 4.473916e9),
-    ("moments", "lognormal_200k"): None,
+    # moments_kernel<float,30>: capture at 50 000 galaxies of the same density, x4
+    # (profiles/moments_kernel_lognormal_50k.md)
+    ("moments", "lognormal_200k"): 4 * (147.244544e6 + 1.073786e9),
     # contract_tc_kernel<Bf16Split>: captures at 50 000 galaxies of each density, x20 and x4
     # (profiles/contract_tc_bf16x3_traffic_50k.md)
     ("contract", "masked_lognormal_1m"): 20 * (1.984181504e9 + 35.843840e6),
