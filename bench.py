@@ -63,8 +63,8 @@ TRAFFIC_BYTES = {
     ("moments", "lognormal_200k"): 4 * (147.244544e6 + 1.073786e9),
     # contract_tc_kernel<Bf16Split>: captures at 50 000 galaxies of each density, x20 and x4
     # (profiles/contract_tc_bf16x3_traffic_50k.md)
-    ("contract", "masked_lognormal_1m"): 20 * (1.984181504e9 + 35.843840e6),
-    ("contract", "lognormal_200k"): 4 * (993.742848e6 + 19.181056e6),
+    ("contract", "masked_lognormal_1m"): 20 * (1.981240576e9 + 35.888640e6),
+    ("contract", "lognormal_200k"): 4 * (993.852928e6 + 19.601408e6),
 }
 TRAFFIC_NOTE = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (profiles/)"
 

@@ -398,10 +398,10 @@ __global__ void __launch_bounds__(kThreads, 2) contract_tc_kernel(const __grid_c
         make_tile(ts, blockIdx.x, a.pair, nz, n_max);
         for (int i = 0; i < kRaw; ++i) {
             mbar_init(smem_u32(&rawfull[i]), 1);
-            mbar_init(smem_u32(&rawempty[i]), 1);
+            mbar_init(smem_u32(&rawempty[i]), kConvWarps);
         }
         for (int i = 0; i < kStages; ++i) {
-            mbar_init(smem_u32(&opfull[i]), 1);
+            mbar_init(smem_u32(&opfull[i]), kConvWarps);
             mbar_init(smem_u32(&opempty[i]), 1);
         }
         for (int i = 0; i < 2; ++i) {
@@ -647,11 +647,11 @@ __global__ void __launch_bounds__(kThreads, 2) contract_tc_kernel(const __grid_c
                             convert(rs, sbase, kend, std::true_type{}, std::false_type{});
                     }
                 }
-                // make the generic-proxy stores visible to the tensor core; once every converter
-                // thread has, hand over the stage and give the raw slot back to the TMA warp
+                // make the generic-proxy stores visible to the tensor core; each warp then hands
+                // over its part of the stage and of the raw slot (the barriers count the warps)
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                conv_all(true);
-                if (tid == 0) {
+                __syncwarp();
+                if (lane == 0) {
                     mbar_arrive(smem_u32(&opfull[st]));
                     mbar_arrive(smem_u32(&rawempty[slot]));
                 }
