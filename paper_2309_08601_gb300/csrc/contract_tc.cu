@@ -163,7 +163,7 @@ struct TileSpec {
     int mapw;            // 0: G moments, 1: W moments
     int ox[2], oy[2];    // order slots of X_s and Y_s
     float xs[2], ys[2];  // +1, or -1 for the complex conjugate
-    float ca, cb, cw;    // c = ca w gamma_1 + cw w + i cb w gamma_2
+    float cb, cw;        // c = -w gamma_1 + i cb w gamma_2 (cw = 0), or c = w (cw = 1)
     int nblk;
     int bl[4], br[4], bg[4], bt[4];  // block: left side, right side, group, 1 = transposed conjugate
 };
@@ -202,7 +202,7 @@ __device__ void make_tile(TileSpec& t, int tile, int pair, int nz, int n_max)
         t.mapw = 0;
         side(0, n - 3 + offg, 1.f, -n - 3 + offg, 1.f);
         side(1, -n - 1 + offg, -1.f, n - 1 + offg, -1.f);
-        t.ca = -1.f, t.cb = -1.f, t.cw = 0.f;
+        t.cb = -1.f, t.cw = 0.f;
         t.nblk = 4;
         block(0, 0, 0, gid(zt, 0, n), 0);
         block(1, 0, 1, gid(zt, 3, n), 0);
@@ -212,7 +212,7 @@ __device__ void make_tile(TileSpec& t, int tile, int pair, int nz, int n_max)
         const int n0 = 2 * (r - n_max - 1);
         t.ns = min(2, 2 * n_max + 1 - n0);
         t.mapw = 1;
-        t.ca = 0.f, t.cb = 0.f, t.cw = 1.f;
+        t.cb = 0.f, t.cw = 1.f;
         t.nblk = t.ns;
         for (int s = 0; s < t.ns; ++s) {
             side(s, n0 + s, 1.f, n0 + s, -1.f);
@@ -221,7 +221,7 @@ __device__ void make_tile(TileSpec& t, int tile, int pair, int nz, int n_max)
     } else {
         t.ns = 1;
         t.nblk = 1;
-        t.ca = -1.f, t.cb = -1.f, t.cw = 0.f;
+        t.cb = -1.f, t.cw = 0.f;
         const int kind = min(4, r / (n_max + 1)), n = kind < 4 ? r % (n_max + 1) : r - 4 * (n_max + 1);
         t.mapw = kind == 4;
         switch (kind) {
@@ -229,7 +229,7 @@ __device__ void make_tile(TileSpec& t, int tile, int pair, int nz, int n_max)
             case 1: side(0, n - 1 + offg, 1.f, -n - 1 + offg, 1.f); t.cb = 1.f; break;  // -(w gamma)^*
             case 2: side(0, -n - 1 + offg, -1.f, -n - 3 + offg, 1.f); break;  // G_{-n-1}^* G_{-n-3}
             case 3: side(0, n - 3 + offg, 1.f, n - 1 + offg, -1.f); break;    // G_{n-3} G_{n-1}^*
-            default: side(0, n, 1.f, n, -1.f); t.ca = 0.f, t.cb = 0.f, t.cw = 1.f; break;  // W_n W_n^*
+            default: side(0, n, 1.f, n, -1.f); t.cb = 0.f, t.cw = 1.f; break;  // W_n W_n^*
         }
         block(0, 0, 0, gid(zt, kind, n), 0);
     }
