@@ -62,10 +62,12 @@ def test_tensor_core_is_deterministic(gpu, noise2k):
             np.testing.assert_array_equal(a[k], b[k])
 
 
-@pytest.mark.parametrize("n_bins,n_max", [(1, 0), (7, 5), (33, 3), (64, 2), (4, 50)])
+@pytest.mark.parametrize("n_bins,n_max", [(1, 0), (7, 5), (31, 4), (32, 3), (33, 3), (64, 2), (4, 50)])
 def test_tile_shapes(gpu, orc, n_bins, n_max):
-    """Groups per tile 8 (n_bins <= 8), 1 with a ragged N (33 bins: 66 rows, N = 96) and the
-    full 128 rows (64 bins); largest order."""
+    """Tiles of two sides (n_bins <= 32: Upsilon_0..3 of one order from four moment rows, N tiles
+    of two orders; 1 bin: 4 of 128 rows; 31 bins: padded bin rows; 32 bins: all 128 rows and
+    N = 128), tiles of one side (33 bins: 66 rows, N = 96; 64 bins: all 128 rows); largest
+    order."""
     rng = np.random.default_rng(100 + n_bins)
     n = 500
     cat = hand_catalog(rng.uniform(0, 20, (n, 2)), rng.normal(0, .3, n) + 1j * rng.normal(0, .3, n),
@@ -79,13 +81,16 @@ def test_tile_shapes(gpu, orc, n_bins, n_max):
         assert rel_err(g["norm"], norm) < ISOLATED_TOL[p], p
 
 
-def test_tomographic_tensor_core(gpu, orc):
-    """n_z = 3: tiles mix Z-triplets; centres of other redshift bins contribute zero rows."""
+@pytest.mark.parametrize("n_bins", [6, 34])
+def test_tomographic_tensor_core(gpu, orc, n_bins):
+    """n_z = 3: every Z-triplet's centre range; with two sides per tile (6 bins) Upsilon_1 of a
+    triplet comes from the tile of the triplet with Z2 and Z3 exchanged, with one side (34 bins)
+    from its own tile."""
     rng = np.random.default_rng(4)
     n = 900
     cat = hand_catalog(rng.uniform(0, 30, (n, 2)), rng.normal(0, .3, n) + 1j * rng.normal(0, .3, n),
                        rng.uniform(0.5, 1.5, n), rng.integers(0, 3, n))
-    setup = dict(n_bins=6, theta_min=0.5, theta_max=10.0, n_max=5, n_z=3)
+    setup = dict(n_bins=n_bins, theta_min=0.5, theta_max=10.0, n_max=5, n_z=3)
     th = [[2.0, 2.0, 2.0]]
     s, r = oracle_run(orc, cat, setup, th)
     for p in TC:
