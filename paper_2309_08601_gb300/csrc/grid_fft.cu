@@ -190,20 +190,21 @@ __global__ void k_fft_gather(int64_t nc, int nk, int j0, int j1, int nbr, const 
                              const cx<T>* __restrict__ P, T scale, int slot0, int dir, size_t plane_rows, int nz,
                              int z, int nbp, int b0, cx<T>* __restrict__ out)
 {
-    const int64_t total = (int64_t)(j1 - j0) * nc;
+    // one output element per thread, the level's bins of a centre on consecutive threads, so a
+    // warp writes whole runs of each centre's row
+    const int64_t total = (int64_t)(j1 - j0) * nc * nbr;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int j = j0 + (int)(t / nc);
-        const int64_t c = t - (int64_t)(j - j0) * nc;
+        const int64_t q = t / nbr;
+        const int bb = (int)(t - q * nbr);
+        const int j = j0 + (int)(q / nc);
+        const int64_t c = q - (int64_t)(j - j0) * nc;
         const int px = cpx[c];
-        cx<T>* o = out + (size_t)(slot0 + dir * j) * plane_rows + ((size_t)c * nz + z) * nbp + b0;
-        for (int bb = 0; bb < nbr; ++bb) {
-            cx<T> v{T(0), T(0)};
-            if (px >= 0) {
-                const cx<T> g = P[((int64_t)bb * nk + j) * grid_plane + px];
-                v = cx<T>{g.x * scale, g.y * scale};
-            }
-            o[bb] = v;
+        cx<T> v{T(0), T(0)};
+        if (px >= 0) {
+            const cx<T> g = P[((int64_t)bb * nk + j) * grid_plane + px];
+            v = cx<T>{g.x * scale, g.y * scale};
         }
+        out[(size_t)(slot0 + dir * j) * plane_rows + ((size_t)c * nz + z) * nbp + b0 + bb] = v;
     }
 }
 
@@ -290,7 +291,7 @@ cudaError_t grid_fft_moments(FftPlanCache* cache, int64_t nc, int nz, int nb, in
                     *what = "inverse cuFFT failed";
                     return cudaErrorUnknown;
                 }
-                k_fft_gather<T><<<fft_blocks((int64_t)(jn - j0) * nc, n_sm), 256, 0, st>>>(
+                k_fft_gather<T><<<fft_blocks((int64_t)(jn - j0) * nc * nbr, n_sm), 256, 0, st>>>(
                     nc, nk, j0, jn, nbr, cpx, plane, P, scale, slot0, dir, plane_rows, nz, z, nbp, b0, out);
                 if ((e = cudaGetLastError()) != cudaSuccess) return e;
             }
