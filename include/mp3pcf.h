@@ -132,11 +132,12 @@ mp3pcf_status mp3pcf_copy_moments(mp3pcf_ctx* ctx, void* d_G, void* d_W);
  * Upsilon_1 += sum_i v_i^* sum_k v_k^2 e^{-2i phi}, Upsilon_2,3 += sum_i v_i sum_k |v_k|^2
  * e^{-2i phi} and N -= sum_i w_i sum_k w_k^2 (v = w gamma), for every order.
  * MP3PCF_FP64 and MP3PCF_FP32 sum on the CUDA cores (tile sums in the moment precision, added in
- * FP64). MP3PCF_FP32_BF16X3 / MP3PCF_FP32_TF32X3 run each group as real GEMMs on the tcgen05
- * tensor cores: every FP32 operand x = hi + lo (hi, lo in BF16 resp. TF32), products
- * hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor memory over 32 (16) centres at a time and
- * per centre slice, slices added in FP64. A bounded wait that gives up in that kernel is
- * reported as ETIMEOUT by the next mp3pcf_counts. */
+ * FP64). MP3PCF_FP32_BF16X3 / MP3PCF_FP32_TF32X3 run the components as real GEMMs over the
+ * centres on the tcgen05 tensor cores (Upsilon_0..3 of one order share a tile and its four moment
+ * rows): every FP32 operand x = hi + lo (hi, lo in BF16 resp. TF32), products
+ * hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor memory over chains of 512 (256) centres,
+ * the chains added in FP32 per centre slice and the slices in FP64 in a fixed order. A bounded
+ * wait that gives up in that kernel is reported as ETIMEOUT by the next mp3pcf_counts. */
 mp3pcf_status mp3pcf_contract_multipoles(mp3pcf_ctx* ctx, double* d_upsilon, double* d_norm);
 
 /* Edge correction, Eqs. ModeCoupling and GammaMultipolesWithEC, Sec. 3.4: per (zt, b1, b2)
